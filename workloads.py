@@ -1,0 +1,77 @@
+"""Named workloads of the DPSNN-STDP step: plain parameter dictionaries.
+
+This module holds only sizes, seeds and model constants; it contains none of
+the method's arithmetic.  Both the CUDA path's binding and the CPU oracle take
+these dictionaries, so it is the one module the two sides share.
+
+Model constants follow the paper (Sec. 2 "Spiking neuron model": 80 % RS / 20 %
+FS Izhikevich neurons; "Projection of synapses with individual delay": delays
+1..20 ms, inhibitory synapses at the minimum delay and local to excitatory
+targets; "Synaptic update": the STDP pair rule), with the column size, fan-out,
+projection mix, initial/maximum weights, STDP amplitudes, long-term plasticity
+constants and thalamic drive of the benchmark workloads below.  Q16 means
+value * 65536 (1 mV = 65536).
+"""
+from __future__ import annotations
+
+import copy
+
+Q16 = 65536
+
+# Parameters shared by every workload (per-column model).
+BASE = dict(
+    neurons_per_col=1250,        # 1000 RS excitatory + 250 FS inhibitory
+    exc_per_col=1000,
+    max_delay_ms=20,
+    w_exc0_q16=6 * Q16,          # +6 mV
+    w_inh0_q16=-5 * Q16,         # -5 mV
+    wmax_q16=10 * Q16,           # 10 mV
+    a_plus_mv=0.1,
+    a_minus_mv=0.12,
+    tau_plus_ms=20.0,
+    tau_minus_ms=20.0,
+    deriv_period_ms=1000,
+    deriv_bias_q16=655,          # 0.01 mV
+    deriv_decay_q16=58982,       # 0.9
+    thal_per_col_per_ms=1,
+    thal_amp_q16=20 * Q16,       # 20 mV
+    flags=0,
+)
+
+WORKLOADS = {
+    # one column, 100 synapses per neuron to random targets of the column
+    "col1_m100": dict(grid_x=1, grid_y=1, fanout=100, pct_ring=(100, 0, 0, 0),
+                      seed=1, sim_ms=1000),
+    # 8x8 torus, 1125 synapses per neuron, 40/30/20/10 projection mix
+    "grid8_m1125": dict(grid_x=8, grid_y=8, fanout=1125, pct_ring=(40, 30, 20, 10),
+                        seed=2, sim_ms=5000),
+    # 64x64 torus (5.12 M neurons, 5.76 G synapses), same mix
+    "grid64_m1125": dict(grid_x=64, grid_y=64, fanout=1125, pct_ring=(40, 30, 20, 10),
+                         seed=3, sim_ms=2000),
+}
+
+
+def workload(name: str, **overrides) -> dict:
+    """Full parameter dictionary of a named workload (a fresh copy)."""
+    cfg = copy.deepcopy(BASE)
+    cfg.update(copy.deepcopy(WORKLOADS[name]))
+    cfg.update(overrides)
+    cfg["name"] = name
+    return cfg
+
+
+def custom(**fields) -> dict:
+    """A parameter dictionary from BASE plus explicit fields (tests, sweeps)."""
+    cfg = copy.deepcopy(BASE)
+    cfg.update(dict(grid_x=1, grid_y=1, fanout=100, pct_ring=(100, 0, 0, 0), seed=1, sim_ms=100))
+    cfg.update(fields)
+    cfg.setdefault("name", "custom")
+    return cfg
+
+
+def n_neurons(cfg: dict) -> int:
+    return cfg["grid_x"] * cfg["grid_y"] * cfg["neurons_per_col"]
+
+
+def n_synapses(cfg: dict) -> int:
+    return n_neurons(cfg) * cfg["fanout"]
