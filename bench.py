@@ -1,0 +1,325 @@
+#!/usr/bin/env python
+"""Benchmark of the DPSNN-STDP per-millisecond step on GB300.
+
+A bench step is one 1 ms step of the whole hot path (delivery + LTD, thalamic
+drive + neuron update, spike compaction + raster, LTP, and the long-term
+plasticity update whenever the step closes a 1000 ms period) on the 64x64
+torus workload (5.12 M neurons, 1125 synapses per neuron, 5.76 G synapses).
+Warm-up steps run first, untimed; then exactly --steps steps are timed with
+CUDA events on the stream the kernels run on.  The value is synaptic events
+per second (one event = one spike reaching one synapse).
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle
+instead, on a bounded sample of the same column model.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+DEFAULT_WORKLOAD = "grid64_m1125"
+# the oracle's bounded sample: same column model and mix on the 8x8 torus,
+# steps [26, 26 + n) (onset of the dense regime), single core
+CPU_SAMPLE_WORKLOAD = "grid8_m1125"
+CPU_SAMPLE_SKIP_MS = 26
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(workloads.WORKLOADS))
+    ap.add_argument("--e2e-steps", type=int, default=None, help="steps of the end-to-end leg (default: --steps)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="bound of the oracle sample")
+    ap.add_argument("--ref-budget-s", type=float, default=150.0, help="wall bound of the reference arm")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
+            int(os.environ.get("WORLD_SIZE", "1")))
+
+
+# ---------------------------------------------------------------------------
+# the oracle's bounded sample (cpu_baseline leg and the reference arm)
+# ---------------------------------------------------------------------------
+def oracle_sample(seconds: float, warmup_steps: int = 0, max_steps: int | None = None):
+    import oracle
+    cfg = workloads.workload(CPU_SAMPLE_WORKLOAD)
+    sim = oracle.Oracle(cfg)
+    sim.run(max(0, CPU_SAMPLE_SKIP_MS - warmup_steps))
+    sim.run(warmup_steps)
+    c0 = sim.counters()
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        sim.run(1)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or (max_steps is not None and steps >= max_steps):
+            break
+    c1 = sim.counters()
+    ev = c1["e_all"] - c0["e_all"]
+    sample = ("oracle on the %s torus (same column model, fan-out and mix), steps %d..%d of its run "
+              "(onset of the dense regime), 1 thread" % (
+                  "8x8", CPU_SAMPLE_SKIP_MS, CPU_SAMPLE_SKIP_MS + steps - 1))
+    return dict(value=ev / el, unit="events/s", cores=1, kind="oracle", sample=sample,
+                steps=steps, seconds=el, events=ev)
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return 0
+    r = oracle_sample(args.ref_budget_s, warmup_steps=args.warmup, max_steps=args.steps)
+    cfg = workloads.workload(args.workload)
+    line = {
+        "impl": "reference", "metric": "synaptic events/s", "value": r["value"], "unit": "events/s",
+        "n_gpus": args.gpus, "steps": r["steps"], "warmup": args.warmup,
+        "ms_per_step": 1000.0 * r["seconds"] / max(1, r["steps"]), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "i32/f32", "data": "synthetic",
+        "config": {"workload": args.workload, "stands_in": "8x8 torus of the same column model (CPU bound)",
+                   "grid": [cfg["grid_x"], cfg["grid_y"]], "fanout": cfg["fanout"]},
+        "cpu_baseline": {"value": r["value"], "unit": "events/s", "cores": 1, "kind": "oracle",
+                         "sample": r["sample"]},
+        "e2e": {"value": r["value"], "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.path = tempfile.mktemp(prefix="clocks_", suffix=".csv")
+        self.proc = None
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    rank, local_rank, world = dist_env()
+    import torch
+    import paper_1310_8478_gb300 as eng
+    from paper_1310_8478_gb300 import snn
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = oracle_sample(args.cpu_seconds)      # before any GPU work; same process, no fork
+
+    eng.build()
+    cfg = workloads.workload(args.workload)
+    K, W = args.steps, args.warmup
+    n_neurons = workloads.n_neurons(cfg)
+    raster_cap = int(n_neurons * (K + W + 2) * 0.8) + (1 << 20)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        t_build = time.perf_counter()
+        net = eng.Network(cfg, stream=stream, raster_capacity=raster_cap)
+        t_build = time.perf_counter() - t_build
+        net.run(W)
+        net.set_profile(True)
+        c0 = net.counters()
+        clocks = ClockSampler(local_rank)
+        barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        net.run(K)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        clk = clocks.stop()
+        ms = e0.elapsed_time(e1)
+        c1 = net.counters()
+        prof = net.profile()
+        net.set_profile(False)
+
+        # end-to-end leg: the same workload restarted, driven from host memory
+        # (the thalamic events of every step are copied in from pinned host
+        # memory, the step's counters are read back)
+        e2e = None
+        if not args.no_e2e:
+            KE = args.e2e_steps if args.e2e_steps is not None else K
+            net.reset()
+            net.set_thalamic(False)
+            stim = snn.snn_thalamic_events(cfg, 0, W + KE)
+            pinned = torch.empty(stim.nbytes, dtype=torch.uint8, pin_memory=True)
+            stim_host = pinned.numpy().view(snn.STIM_DTYPE)
+            stim_host[:] = stim
+            per_step = cfg["grid_x"] * cfg["grid_y"] * cfg["thal_per_col_per_ms"]
+            for s in range(W):
+                net.run_host_counts(1, stim_host[s * per_step:(s + 1) * per_step])
+            net.raster_reset()
+            ce0 = net.counters()
+            barrier()
+            t0 = time.perf_counter()
+            for s in range(W, W + KE):
+                net.run_host_counts(1, stim_host[s * per_step:(s + 1) * per_step])
+                net.counters()
+            el = time.perf_counter() - t0
+            barrier()
+            ce1 = net.counters()
+            e2e = {"value": (ce1["e_all"] - ce0["e_all"]) / el, "unit": "events/s",
+                   "h2d_bytes_per_step": per_step * snn.STIM_DTYPE.itemsize,
+                   "d2h_bytes_per_step": 3 * ctypes_sizeof_counters(), "steps": KE,
+                   "bitexact_with_device_run": bool(ce1["e_all"] - ce0["e_all"] == c1["e_all"] - c0["e_all"]
+                                                    and KE == K)}
+        net.close()
+
+    d_events = c1["e_all"] - c0["e_all"]
+    d_exc = c1["e_exc"] - c0["e_exc"]
+    d_ltp = c1["l_exc"] - c0["l_exc"]
+    d_spikes = c1["spikes"] - c0["spikes"]
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        ev = torch.tensor([d_events], dtype=torch.float64, device="cuda")
+        dist.all_reduce(ev)
+        total_events = float(ev.item())
+    else:
+        total_events = float(d_events)
+    if rank != 0:
+        return 0
+
+    secs = ms / 1000.0
+    value = total_events / secs
+    rate_hz = d_spikes / n_neurons / (K / 1000.0)
+    n_exc_syn = cfg["grid_x"] * cfg["grid_y"] * cfg["exc_per_col"] * cfg["fanout"]
+    # algorithmic bytes per launch of each kernel (measurement)
+    n_deriv = prof["deriv"][0]
+    alg = {
+        "deliver": (8.0 * d_events + 8.0 * d_exc) / max(1, prof["deliver"][0]),
+        "ltp": 12.0 * d_ltp / max(1, prof["ltp"][0]),
+        "neuron": 32.0 * n_neurons,
+        "deriv": 16.0 * n_exc_syn,
+    }
+    peak, peak_kind = measured_peaks()
+    kernel_ms = {k: prof[k][1] for k in ("deliver", "neuron", "ltp", "deriv")}
+    dom = max(kernel_ms, key=kernel_ms.get)
+    avg_ms = prof[dom][1] / max(1, prof[dom][0])
+    achieved = alg[dom] / (avg_ms / 1000.0) / 1e9
+    per_kernel = {k: {"launches": prof[k][0], "ms": round(prof[k][1], 3),
+                      "share": round(prof[k][1] / max(1e-9, sum(kernel_ms.values())), 4),
+                      "alg_gbs": round(alg[k] / (prof[k][1] / max(1, prof[k][0]) / 1000.0) / 1e9, 1)
+                      if prof[k][0] else None}
+                  for k in ("deliver", "neuron", "ltp", "deriv")}
+    line = {
+        "metric": "synaptic events/s", "value": value, "unit": "events/s", "n_gpus": world, "steps": K,
+        "warmup": W, "ms_per_step": ms / K, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "i32/f32", "data": "synthetic",
+        "config": {"workload": "%s: %dx%d torus, %d neurons, M=%d, %d synapses, mix %s" % (
+            args.workload, cfg["grid_x"], cfg["grid_y"], n_neurons, cfg["fanout"], workloads.n_synapses(cfg),
+            "/".join(str(p) for p in cfg["pct_ring"])),
+            "step": "1 ms of simulated time", "parallelism": "replicas" if world > 1 else "single GPU",
+            "l2": "inputs larger than L2 (synapse arrays ~%.0f GB resident)" % (workloads.n_synapses(cfg) * 12 / 1e9),
+            "sim_ms_timed": [W, W + K]},
+        "wall_s_per_sim_s_per_hz": (secs / (K / 1000.0)) / rate_hz if rate_hz > 0 else None,
+        "wall_s_per_sim_s": secs / (K / 1000.0),
+        "rate_hz": rate_hz,
+        "events": d_events, "spikes": d_spikes,
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "traffic": None},
+        "kernels": per_kernel,
+        "gpu_launches": int(sum(prof[k][0] for k in ("deliver", "neuron", "ltp", "deriv"))),
+        "build_s": round(t_build, 2),
+        "e2e": e2e,
+        "cpu_baseline": None if cpu is None else {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")},
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def ctypes_sizeof_counters():
+    # snn_run_host reads the device counters before and after; the step's
+    # metric is then read once more through snn_read_counters
+    return 104
+
+
+if __name__ == "__main__":
+    sys.exit(main())

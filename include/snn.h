@@ -1,0 +1,298 @@
+/*
+ * snn.h -- C ABI of the GB300 engine for the DPSNN-STDP per-millisecond step
+ * (Paolucci et al., "Distributed simulation of polychronous and plastic
+ * spiking neural networks", arXiv 1310.8478).
+ *
+ * One step of simulated time (1 ms) runs, on the device, the paper's cycle
+ * (Sec. 2 "Mixed time-driven and event driven simulation", steps 2.1-2.7) in
+ * the order
+ *   S1 delivery of the axonal spikes due now through the delay-bucketed
+ *      synapse lists, current injection and long-term depression (2.3-2.6);
+ *   S2 thalamic drive and Izhikevich update of every neuron (2.7);
+ *   S3 compaction of the neurons that fired into the axonal-delay ring and
+ *      the rastergram (2.2);
+ *   S4 long-term potentiation of the incoming synapses of every neuron that
+ *      fired (2.1);
+ *   S5 at the end of every plasticity period, the long-term update
+ *      w += bias + sd (clamped to [0, wmax]), sd *= decay (Table 2,
+ *      "long term synaptic plasticity").
+ *
+ * Conventions for every call:
+ *   - Pointers named host_* or documented as host memory are ordinary host
+ *     buffers owned by the caller; the library never keeps them.
+ *   - The library owns the snn_net handle and all device memory behind it
+ *     (allocated with cudaMalloc on the current device, or through the
+ *     allocator installed by snn_set_allocator).
+ *   - Return value: SNN_OK (0) or a negative SNN_E* code; snn_strerror gives a
+ *     message.  A failed call leaves the handle usable unless it returned
+ *     SNN_ECUDA.
+ *   - Fixed point: weights, currents and synaptic derivatives are int32 with
+ *     16 fractional bits ("Q16"; 1 mV = 65536).
+ *   - Neuron ids: gid = column * neurons_per_col + local, column = y * grid_x
+ *     + x; local ids below exc_per_col are excitatory (RS), the rest
+ *     inhibitory (FS) (Sec. 2 "Spiking neuron model").
+ */
+#ifndef SNN_H
+#define SNN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SNN_OK 0
+#define SNN_EINVAL (-1)     /* bad argument or configuration */
+#define SNN_ENOMEM (-2)     /* device budget exceeded or allocation failed */
+#define SNN_ECUDA (-3)      /* CUDA runtime error; the handle must be freed */
+#define SNN_EOVERFLOW (-4)  /* the int32 Q16 current bound cannot be guaranteed */
+#define SNN_ETIMEOUT (-5)   /* a bounded device-side wait gave up */
+#define SNN_ETRUNC (-6)     /* output buffer too small; *n_out holds the size needed */
+#define SNN_ESTATE (-7)     /* the call does not fit the handle's state */
+
+/* cfg.flags */
+#define SNN_STDP_OFF 1u      /* no depression / potentiation (sd stays 0) */
+#define SNN_DELIVERY_OFF 2u  /* spikes are not delivered (neurons see drive only) */
+
+/*
+ * Network and model configuration (plain old data).
+ * Topology: Sec. 2 "Bidimensional arrays of neural columns" (toroidal grid of
+ * columns; excitatory neurons project to their own column and to the 1st, 2nd
+ * and 3rd rings of neighbours, inhibitory neurons only to excitatory neurons
+ * of their own column) and "Projection of synapses with individual delay"
+ * (M forward synapses per neuron; excitatory delays uniform in
+ * 1..max_delay_ms, inhibitory delays 1 ms).  STDP: Sec. 2 "Synaptic update"
+ * equation, A+/A- in mV, tau in ms.
+ */
+typedef struct {
+    uint32_t grid_x, grid_y;             /* columns on the torus */
+    uint32_t neurons_per_col;            /* >= 2 */
+    uint32_t exc_per_col;                /* 1..neurons_per_col */
+    uint32_t fanout;                     /* M synapses per neuron, 1..65535 */
+    uint32_t pct_ring[4];                /* % of M: own column, ring 1, 2, 3; sum 100 */
+    uint32_t max_delay_ms;               /* 1..31 */
+    int32_t w_exc0_q16, w_inh0_q16;      /* initial weights */
+    int32_t wmax_q16;                    /* excitatory weights are clamped to [0, wmax] */
+    double a_plus_mv, a_minus_mv;        /* A+ (added) and A- (subtracted), both >= 0 */
+    double tau_plus_ms, tau_minus_ms;
+    uint32_t deriv_period_ms;            /* long-term update period; 0 = never */
+    int32_t deriv_bias_q16;              /* added to w at each update */
+    int32_t deriv_decay_q16;             /* sd = (sd * decay + 2^15) >> 16 */
+    uint32_t thal_per_col_per_ms;        /* thalamic events per column per ms */
+    int32_t thal_amp_q16;                /* current of one thalamic event */
+    uint64_t seed;                       /* key of the Philox4x32-10 draws */
+    uint32_t flags;                      /* SNN_STDP_OFF | SNN_DELIVERY_OFF */
+    uint32_t reserved;                   /* must be 0 */
+    uint64_t raster_capacity;            /* spikes kept on the device; 0 = no raster */
+} snn_config;
+
+typedef struct { int32_t t_ms; int32_t gid; } snn_spike;
+
+/* External current event: adds q16 to neuron gid's input at step t. */
+typedef struct { int32_t t; int32_t gid; int32_t q16; } snn_stimulus;
+
+typedef struct {
+    int64_t t;               /* steps simulated so far */
+    int64_t spikes;          /* all spikes emitted */
+    int64_t e_all;           /* synaptic events delivered (spike x synapse) */
+    int64_t e_exc;           /* of which on excitatory (plastic) synapses */
+    int64_t l_exc;           /* potentiation visits: sum over spikes of excitatory in-degree */
+    int64_t raster_kept;     /* spikes stored in the device raster */
+    int64_t raster_dropped;  /* spikes not stored because the raster was full */
+    int32_t error;           /* device error word (0 = none) */
+    int32_t reserved;
+} snn_counters;
+
+/*
+ * Launch shape of the step kernels.  Any shape gives bit-identical results
+ * (integer accumulation; the spike lists' order does not matter).
+ * Zero fields keep the current value.
+ */
+typedef struct {
+    uint32_t deliver_block;          /* threads per block of S1 (multiple of 32) */
+    uint32_t deliver_blocks_per_sm;
+    uint32_t neuron_block;           /* threads per block of S2/S3 */
+    uint32_t ltp_block;              /* threads per block of S4 */
+    uint32_t ltp_blocks_per_sm;
+    uint32_t deriv_block;
+    uint32_t graph_steps;            /* steps per captured CUDA graph; even; 0 = keep, 1 = no graphs */
+    uint32_t reserved;
+} snn_launch;
+
+/* Per-kernel device time collected while profiling is on (CUDA events). */
+typedef struct {
+    int64_t launches[5];             /* deliver, neuron, ltp, deriv, other */
+    double ms[5];
+} snn_profile;
+
+typedef struct snn_net snn_net;
+
+/*
+ * snn_build_network -- construct the network of cfg on the current device
+ * (Sec. 2 "Initial construction" and "Distributed generation of reproducible
+ * connections"): for every source gid and ordinal j, Philox4x32-10 with key
+ * (seed low, seed high) and counter (gid, j, 0, 0) draws the target neuron and
+ * the delay, so the network does not depend on the device layout.  Builds the
+ * delay-bucketed forward lists, the reverse (incoming excitatory) index and
+ * the initial state (v = -65 mV, u = 0.2 v).
+ *   cuda_stream: cudaStream_t the engine works on (NULL: a private stream).
+ *   hbm_budget_bytes: upper bound of device memory the net may use (0: no bound).
+ *   out: receives the handle.
+ * Errors: SNN_EINVAL (bad cfg), SNN_ENOMEM (footprint above the budget or
+ * allocation failure), SNN_EOVERFLOW (in-degree * wmax + drive may exceed
+ * int32), SNN_ECUDA.
+ */
+int snn_build_network(const snn_config *cfg, void *cuda_stream, size_t hbm_budget_bytes,
+                      snn_net **out);
+
+/*
+ * snn_build_network_explicit -- same, from explicit host synapse lists in
+ * canonical order (Sec. 2 "Projection of synapses": each source i owns
+ * synapses (D, W, K)): source p owns host_tgt/host_delay/host_w[row_off[p]
+ * .. row_off[p+1]), N = grid_x * grid_y * neurons_per_col.  cfg.fanout,
+ * pct_ring and seed are ignored for the topology (seed still keys the
+ * thalamic drive).  Rows may be empty; a row holds at most 65535 synapses.
+ */
+int snn_build_network_explicit(const snn_config *cfg, const int64_t *host_row_off,
+                               const int32_t *host_tgt, const uint8_t *host_delay,
+                               const int32_t *host_w, void *cuda_stream,
+                               size_t hbm_budget_bytes, snn_net **out);
+
+/*
+ * snn_set_stimulus -- external current events (host array, any order; n may
+ * be 0 to clear), applied in S2 of their step before the neuron update.  The
+ * thalamic drive of Sec. 2 / Table 2 ("thalamic input") is separate and
+ * always on unless thal_per_col_per_ms = 0.  Events before the current step
+ * are ignored.  SNN_EINVAL if a gid is out of range.
+ */
+int snn_set_stimulus(snn_net *net, const snn_stimulus *host_events, size_t n);
+
+/*
+ * snn_set_thalamic -- on = 0: the net stops drawing its own thalamic events
+ * (the caller then supplies the drive, e.g. snn_thalamic_events through
+ * snn_run_host); on = 1: back to cfg.thal_per_col_per_ms events per column.
+ */
+int snn_set_thalamic(snn_net *net, int on);
+
+/* snn_set_launch / snn_get_launch -- launch shape (see snn_launch). */
+int snn_set_launch(snn_net *net, const snn_launch *launch);
+int snn_get_launch(const snn_net *net, snn_launch *launch);
+
+/*
+ * snn_step -- advance one millisecond (S1..S5 above).  Enqueued on the net's
+ * stream; returns after the step has completed and the device error word has
+ * been checked.
+ */
+int snn_step(snn_net *net);
+
+/*
+ * snn_run -- advance n_ms steps (CUDA-graph replays of graph_steps steps where
+ * the alignment allows, single steps otherwise); returns after completion and
+ * the error-word check.
+ */
+int snn_run(snn_net *net, uint32_t n_ms);
+
+/*
+ * snn_run_host -- the end-to-end call for a caller that lives in host memory:
+ * copies host_stimulus (n_stim events, may be NULL) to the device as the
+ * external stimulus of the coming steps, advances n_ms steps and, if
+ * host_spikes is not NULL, copies the spikes of those steps, sorted by
+ * (t, gid), into host_spikes (capacity cap) and resets the device raster.
+ * *n_out = spikes emitted in the window.  SNN_ETRUNC if cap is too small (the
+ * simulation still advanced) or the device raster overflowed.
+ */
+int snn_run_host(snn_net *net, uint32_t n_ms, const snn_stimulus *host_stimulus, size_t n_stim,
+                 snn_spike *host_spikes, size_t cap, size_t *n_out);
+
+/*
+ * snn_read_raster -- rastergram (Sec. 2 "Production of observables") of steps
+ * [t0, t1): host_buf receives (t, gid) sorted by t then gid; cap entries at
+ * most; *n_out = entries in the window.  SNN_ETRUNC if cap < *n_out or part
+ * of the window was dropped because the device raster was full.
+ */
+int snn_read_raster(snn_net *net, int32_t t0, int32_t t1, snn_spike *host_buf, size_t cap,
+                    size_t *n_out);
+
+/* snn_raster_reset -- forget the stored raster (frees room for later steps). */
+int snn_raster_reset(snn_net *net);
+
+/*
+ * snn_read_synapses -- synapses of sources [first, first + count) in canonical
+ * (source, ordinal) order; any host pointer may be NULL.  *n_out = synapses in
+ * the range; SNN_ETRUNC if cap is smaller.  Inhibitory synapses keep their
+ * weight and sd = 0.
+ */
+int snn_read_synapses(snn_net *net, uint32_t first, uint32_t count, int32_t *host_tgt,
+                      uint8_t *host_delay, int32_t *host_w, int32_t *host_sd, size_t cap,
+                      size_t *n_out);
+
+/* snn_read_weights -- w and sd of every synapse, canonical order (cap >= synapses). */
+int snn_read_weights(snn_net *net, int32_t *host_w, int32_t *host_sd, size_t cap, size_t *n_out);
+
+/* snn_read_neurons -- v and u of neurons [first, first + count) (host, may be NULL). */
+int snn_read_neurons(snn_net *net, uint32_t first, uint32_t count, float *host_v, float *host_u);
+
+/* snn_read_counters -- event counters and the device error word. */
+int snn_read_counters(snn_net *net, snn_counters *out);
+
+/* snn_net_info -- neurons, synapses, device bytes held. */
+int snn_net_info(const snn_net *net, uint32_t *n_neurons, int64_t *n_synapses,
+                 size_t *device_bytes);
+
+/* snn_set_profile -- 1: time every kernel with CUDA events (no graphs); 0: off. */
+int snn_set_profile(snn_net *net, int on);
+int snn_read_profile(snn_net *net, snn_profile *out);
+
+/*
+ * snn_save_state / snn_load_state -- checkpoint of the dynamic state (t,
+ * neurons, spike history, ring, weights, derivatives, counters, raster step
+ * offsets) into / from a host buffer.  Call with host_buf NULL to get the
+ * size in *n.  Loading needs a net built from the same configuration.
+ */
+int snn_save_state(snn_net *net, void *host_buf, size_t cap, size_t *n);
+int snn_load_state(snn_net *net, const void *host_buf, size_t n);
+
+/*
+ * snn_reset -- return a generated net to its initial state (t = 0, initial
+ * weights, sd = 0, v = -65 mV, u = 0.2 v, empty ring and raster, counters 0)
+ * without rebuilding it; external stimulus is cleared.  SNN_ESTATE for nets
+ * built from explicit lists (their initial weights are not kept).
+ */
+int snn_reset(snn_net *net);
+
+/*
+ * snn_thalamic_events -- the thalamic drive of cfg for steps [t0, t0 + n_ms)
+ * as host events (Sec. 2 "Distributed generation of reproducible ... external
+ * 'thalamic' stimulus": per column and step, thal_per_col_per_ms events, the
+ * k-th on neuron floor(r0 * neurons_per_col / 2^32) of Philox4x32-10 with key
+ * (seed low, seed high) and counter (t, column, 1, k)), sorted by step.
+ * A net built with thal_per_col_per_ms = 0 that receives these events through
+ * snn_set_stimulus / snn_run_host evolves bit-identically to one that draws
+ * them itself.  Host-only computation; needs no GPU.  *n_out = number of
+ * events; SNN_ETRUNC if cap is smaller (host_events may then be NULL).
+ */
+int snn_thalamic_events(const snn_config *cfg, int32_t t0, uint32_t n_ms, snn_stimulus *host_events,
+                        size_t cap, size_t *n_out);
+
+/* snn_free -- release the handle and its device memory (NULL is allowed). */
+void snn_free(snn_net *net);
+
+/* snn_strerror -- static message of an SNN_E* code. */
+const char *snn_strerror(int code);
+
+/* snn_last_error -- message of the last failure in this thread (never NULL). */
+const char *snn_last_error(void);
+
+/*
+ * snn_set_allocator -- route device allocations of nets built afterwards
+ * through alloc(bytes, stream, ctx) / release(ptr, ctx) (e.g. a framework's
+ * caching allocator).  NULL restores cudaMalloc / cudaFree.
+ */
+void snn_set_allocator(void *(*alloc)(size_t bytes, void *stream, void *ctx),
+                       void (*release)(void *ptr, void *ctx), void *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,1199 @@
+// snn_api.cu -- host engine and C ABI of the GB300 DPSNN-STDP step (include/snn.h).
+//
+// Owns the device layout of one network, the construction sequence (device
+// generation, in-degree count, prefix sum, reverse-index scatter), the step
+// sequence (eager launches or CUDA-graph replays of graph_steps steps), the
+// readers and the checkpoint format.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "snn_internal.cuh"
+
+using namespace snn;
+
+namespace {
+
+thread_local std::string g_last_error = "";
+
+void set_error(const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+}
+
+void *(*g_alloc)(size_t, void *, void *) = nullptr;
+void (*g_release)(void *, void *) = nullptr;
+void *g_alloc_ctx = nullptr;
+
+#define SNN_CUDA(call)                                                                   \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess) {                                                         \
+            set_error("%s failed: %s", #call, cudaGetErrorString(e_));                   \
+            return SNN_ECUDA;                                                            \
+        }                                                                                \
+    } while (0)
+
+#define SNN_TRY(expr)                                                                    \
+    do {                                                                                 \
+        int r_ = (expr);                                                                 \
+        if (r_ != SNN_OK) return r_;                                                     \
+    } while (0)
+
+constexpr uint32_t kStateMagic = 0x534e4e31u;  // "SNN1"
+
+__global__ void k_fill_row_off(int64_t *row_off, uint32_t n, uint32_t m)
+{
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += gridDim.x * blockDim.x)
+        row_off[i] = (int64_t)i * m;
+}
+
+}  // namespace
+
+struct WeightRange {
+    int32_t exc_min, exc_max, inh_min, inh_max;   // initial weights by source kind
+};
+
+struct snn_net {
+    snn_config cfg{};
+    WeightRange wrange{};
+    int device = 0;
+    int sm_count = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    bool explicit_net = false;
+    GenParams gen{};
+    DevNet dn{};
+    uint32_t N = 0;
+    int64_t S = 0;
+    int64_t n_rin = 0;
+    size_t budget = 0;
+    size_t bytes_held = 0;
+    struct Block { void *p; size_t bytes; };
+    std::vector<Block> blocks;
+    void *(*alloc)(size_t, void *, void *) = nullptr;
+    void (*release)(void *, void *) = nullptr;
+    void *alloc_ctx = nullptr;
+    // device arrays (also reachable through dn)
+    int64_t *row_off = nullptr;
+    uint16_t *doff = nullptr;
+    int32_t *tgt = nullptr, *w = nullptr, *sd = nullptr;
+    uint8_t *canon_delay = nullptr;
+    int64_t *rin_off = nullptr;
+    uint64_t *rin = nullptr;
+    DevCounters *ctr = nullptr;
+    int32_t *lut = nullptr;
+    int64_t raster_steps_cap = 0;   // entries of dn.raster_step_off
+    // stimulus
+    size_t stim_cap = 0;
+    int64_t stim_off_cap = 0;
+    // host state
+    int32_t t = 0;
+    snn_launch launch{};
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    uint32_t graph_len = 0;
+    bool graphs_dirty = true;
+    bool profile = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<int> ev_kind;
+    size_t ev_used = 0;
+    double prof_ms[kKinds] = {0};
+    int64_t prof_n[kKinds] = {0};
+};
+
+namespace {
+
+int dalloc(snn_net *net, size_t bytes, void **out)
+{
+    *out = nullptr;
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~size_t(255);
+    if (net->budget && net->bytes_held + bytes > net->budget) {
+        set_error("device budget exceeded: %zu + %zu > %zu bytes", net->bytes_held, bytes, net->budget);
+        return SNN_ENOMEM;
+    }
+    void *p = nullptr;
+    if (net->alloc) {
+        p = net->alloc(bytes, (void *)net->stream, net->alloc_ctx);
+        if (!p) {
+            set_error("allocator hook failed for %zu bytes", bytes);
+            return SNN_ENOMEM;
+        }
+    } else {
+        cudaError_t e = cudaMalloc(&p, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            set_error("cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+            return SNN_ENOMEM;
+        }
+    }
+    net->blocks.push_back({p, bytes});
+    net->bytes_held += bytes;
+    *out = p;
+    return SNN_OK;
+}
+
+void dfree(snn_net *net, void *p)
+{
+    if (!p) return;
+    for (size_t i = 0; i < net->blocks.size(); ++i) {
+        if (net->blocks[i].p == p) {
+            if (net->release) net->release(p, net->alloc_ctx);
+            else cudaFree(p);
+            net->bytes_held -= net->blocks[i].bytes;
+            net->blocks.erase(net->blocks.begin() + (long)i);
+            return;
+        }
+    }
+}
+
+template <typename T>
+int dalloc_t(snn_net *net, size_t count, T **out)
+{
+    void *p = nullptr;
+    int r = dalloc(net, count * sizeof(T), &p);
+    *out = (T *)p;
+    return r;
+}
+
+void drop_graphs(snn_net *net)
+{
+    for (int i = 0; i < 2; ++i) {
+        if (net->graph[i]) cudaGraphExecDestroy(net->graph[i]);
+        net->graph[i] = nullptr;
+    }
+    net->graphs_dirty = true;
+}
+
+int check_config(const snn_config *c)
+{
+    if (!c) { set_error("cfg is NULL"); return SNN_EINVAL; }
+    if (c->grid_x == 0 || c->grid_y == 0) { set_error("grid must be at least 1x1"); return SNN_EINVAL; }
+    if (c->neurons_per_col < 2 || c->exc_per_col == 0 || c->exc_per_col > c->neurons_per_col) {
+        set_error("need neurons_per_col >= 2 and 1 <= exc_per_col <= neurons_per_col");
+        return SNN_EINVAL;
+    }
+    const uint64_t n = (uint64_t)c->grid_x * c->grid_y * c->neurons_per_col;
+    if (n > 0x7fffffffull) { set_error("too many neurons (%llu)", (unsigned long long)n); return SNN_EINVAL; }
+    if ((uint64_t)c->grid_x * c->grid_y > 65535u) { set_error("at most 65535 columns"); return SNN_EINVAL; }
+    if (c->fanout == 0 || c->fanout > 65535u) { set_error("fanout must be 1..65535"); return SNN_EINVAL; }
+    if (c->pct_ring[0] + c->pct_ring[1] + c->pct_ring[2] + c->pct_ring[3] != 100) {
+        set_error("pct_ring must sum to 100");
+        return SNN_EINVAL;
+    }
+    if (c->max_delay_ms < 1 || c->max_delay_ms > 31) { set_error("max_delay_ms must be 1..31"); return SNN_EINVAL; }
+    if (c->wmax_q16 < 0) { set_error("wmax must be >= 0"); return SNN_EINVAL; }
+    if (!(c->a_plus_mv >= 0) || !(c->a_minus_mv >= 0) || !(c->tau_plus_ms > 0) || !(c->tau_minus_ms > 0)) {
+        set_error("STDP amplitudes must be >= 0 and time constants > 0");
+        return SNN_EINVAL;
+    }
+    if (c->reserved != 0) { set_error("reserved field must be 0"); return SNN_EINVAL; }
+    if (c->flags & ~(SNN_STDP_OFF | SNN_DELIVERY_OFF)) { set_error("unknown flags"); return SNN_EINVAL; }
+    if (c->deriv_period_ms > 0x3fffffffu) { set_error("deriv_period_ms too large"); return SNN_EINVAL; }
+    return SNN_OK;
+}
+
+// STDP amounts of the pair rule (Sec. 2 "Synaptic update" equation), rounded
+// to Q16; the table must cover every non-zero amount.
+int build_luts(const snn_config *c, std::vector<int32_t> &lut)
+{
+    lut.assign(2 * kLut, 0);
+    const double amp[2] = {c->a_plus_mv, c->a_minus_mv};
+    const double tau[2] = {c->tau_plus_ms, c->tau_minus_ms};
+    for (int s = 0; s < 2; ++s) {
+        for (int k = 0; k <= kLut; ++k) {
+            const double x = amp[s] * std::exp(-(double)k / tau[s]) * 65536.0;
+            const long long q = std::llround(x);
+            if (k == kLut) {
+                if (q != 0) {
+                    set_error("STDP window longer than %d ms (amount at lag %d is %lld)", kLut, kLut, q);
+                    return SNN_EINVAL;
+                }
+            } else {
+                if (q > 0x3fffffff) { set_error("STDP amplitude too large"); return SNN_EINVAL; }
+                lut[s * kLut + k] = (int32_t)q;
+            }
+        }
+    }
+    return SNN_OK;
+}
+
+int grid_for(const snn_net *net, uint32_t per_sm)
+{
+    return std::max(1, net->sm_count) * (int)std::max(1u, per_sm);
+}
+
+// footprint of everything but the raster (bytes)
+size_t footprint(const snn_config *c, uint32_t N, int64_t S, int64_t n_rin, bool explicit_net)
+{
+    const size_t D = c->max_delay_ms;
+    size_t b = 0;
+    b += (size_t)S * 12;                          // tgt, w, sd
+    b += (size_t)N * kDoffStride * 2;             // delay offsets
+    b += ((size_t)N + 1) * 8 * 2;                 // row_off, rin_off
+    b += (size_t)n_rin * 8;                       // reverse index
+    b += (size_t)N * 24;                          // v u I hist last_old last_spike
+    b += D * N * 4 + D * 8;                       // ring
+    b += (size_t)N * 12 + ((size_t)N / 1024 + 2) * 8;  // build scratch
+    if (explicit_net) b += (size_t)S;             // canonical delays
+    b += 64 * 1024;
+    return b;
+}
+
+int alloc_common(snn_net *net)
+{
+    const uint32_t N = net->N;
+    const uint32_t D = net->cfg.max_delay_ms;
+    DevNet &dn = net->dn;
+    SNN_TRY(dalloc_t(net, (size_t)net->S, &net->tgt));
+    SNN_TRY(dalloc_t(net, (size_t)net->S, &net->w));
+    SNN_TRY(dalloc_t(net, (size_t)net->S, &net->sd));
+    SNN_TRY(dalloc_t(net, (size_t)N * kDoffStride, &net->doff));
+    SNN_TRY(dalloc_t(net, (size_t)N + 1, &net->row_off));
+    SNN_TRY(dalloc_t(net, (size_t)N + 1, &net->rin_off));
+    SNN_TRY(dalloc_t(net, (size_t)N, &dn.v));
+    SNN_TRY(dalloc_t(net, (size_t)N, &dn.u));
+    SNN_TRY(dalloc_t(net, (size_t)N, &dn.I));
+    SNN_TRY(dalloc_t(net, (size_t)N, &dn.hist));
+    SNN_TRY(dalloc_t(net, (size_t)N, &dn.last_old));
+    SNN_TRY(dalloc_t(net, (size_t)N, &dn.last_spike));
+    SNN_TRY(dalloc_t(net, (size_t)D * N, &dn.ring_ids));
+    SNN_TRY(dalloc_t(net, (size_t)2 * D, &dn.ring_cnt));
+    SNN_TRY(dalloc_t(net, 1, &net->ctr));
+    SNN_TRY(dalloc_t(net, (size_t)2 * kLut, &net->lut));
+    if (net->cfg.raster_capacity) {
+        SNN_TRY(dalloc_t(net, (size_t)net->cfg.raster_capacity, &dn.raster_gid));
+        net->raster_steps_cap = 1 << 14;
+        SNN_TRY(dalloc_t(net, (size_t)net->raster_steps_cap, &dn.raster_step_off));
+    }
+    dn.N = N;
+    dn.npc = net->cfg.neurons_per_col;
+    dn.ne = net->cfg.exc_per_col;
+    dn.C = net->cfg.grid_x * net->cfg.grid_y;
+    dn.D = D;
+    dn.S = net->S;
+    dn.row_off = net->row_off;
+    dn.doff = net->doff;
+    dn.tgt = net->tgt;
+    dn.w = net->w;
+    dn.sd = net->sd;
+    dn.rin_off = net->rin_off;
+    dn.raster_cap = net->cfg.raster_capacity;
+    dn.raster_t0 = 0;
+    dn.lut_p = net->lut;
+    dn.lut_m = net->lut + kLut;
+    dn.stim_t0 = dn.stim_t1 = 0;
+    dn.ctr = net->ctr;
+    dn.thal_per_col = net->cfg.thal_per_col_per_ms;
+    dn.thal_amp = net->cfg.thal_amp_q16;
+    dn.seed_lo = (uint32_t)(net->cfg.seed & 0xffffffffu);
+    dn.seed_hi = (uint32_t)(net->cfg.seed >> 32);
+    dn.flags = net->cfg.flags;
+    dn.deriv_bias = net->cfg.deriv_bias_q16;
+    dn.deriv_decay = net->cfg.deriv_decay_q16;
+    dn.wmax = net->cfg.wmax_q16;
+    return SNN_OK;
+}
+
+// in-degrees -> overflow check -> reverse index -> LUTs -> initial state
+int finish_build(snn_net *net)
+{
+    const uint32_t N = net->N;
+    cudaStream_t s = net->stream;
+    DevNet &dn = net->dn;
+    int32_t *indeg_exc = nullptr, *indeg_inh = nullptr, *cursor = nullptr, *mx = nullptr;
+    long long *sums = nullptr;
+    const uint32_t scan_blocks = (N + 1023) / 1024;
+    SNN_TRY(dalloc_t(net, (size_t)N, &indeg_exc));
+    SNN_TRY(dalloc_t(net, (size_t)N, &indeg_inh));
+    SNN_TRY(dalloc_t(net, (size_t)N, &cursor));
+    SNN_TRY(dalloc_t(net, 2, &mx));
+    SNN_TRY(dalloc_t(net, (size_t)scan_blocks + 1, &sums));
+    SNN_CUDA(cudaMemsetAsync(indeg_exc, 0, (size_t)N * 4, s));
+    SNN_CUDA(cudaMemsetAsync(indeg_inh, 0, (size_t)N * 4, s));
+    SNN_CUDA(cudaMemsetAsync(cursor, 0, (size_t)N * 4, s));
+    SNN_CUDA(cudaMemsetAsync(mx, 0, 8, s));
+    const int g = grid_for(net, 8);
+    k_count_indeg<<<g, 256, 0, s>>>(dn, indeg_exc, indeg_inh);
+    k_max2<<<g, 256, 0, s>>>(indeg_exc, indeg_inh, N, mx);
+    int32_t hmx[2] = {0, 0};
+    SNN_CUDA(cudaMemcpyAsync(hmx, mx, 8, cudaMemcpyDeviceToHost, s));
+    SNN_CUDA(cudaStreamSynchronize(s));
+    // Q16 current bound: every synapse of the busiest target at its extreme
+    // weight plus all the thalamic drive of its column must stay in int32
+    // (excitatory weights move inside [0, max(wmax, initial)], inhibitory
+    // weights never change).
+    {
+        const snn_config &c = net->cfg;
+        const WeightRange &r = net->wrange;
+        const long long thal = (long long)c.thal_per_col_per_ms * c.thal_amp_q16;
+        const long long pos = (long long)hmx[0] * std::max<long long>(c.wmax_q16, r.exc_max) +
+                              (long long)hmx[1] * std::max<long long>(0, r.inh_max) + std::max(0ll, thal);
+        const long long neg = (long long)hmx[0] * std::max<long long>(0, -(long long)r.exc_min) +
+                              (long long)hmx[1] * std::max<long long>(0, -(long long)r.inh_min) +
+                              std::max(0ll, -thal);
+        if (pos > 0x7fffffffll || neg > 0x80000000ll) {
+            set_error("int32 Q16 current bound violated (max exc in-degree %d, inh in-degree %d)", hmx[0], hmx[1]);
+            return SNN_EOVERFLOW;
+        }
+    }
+    k_scan_sums<<<scan_blocks, 256, 0, s>>>(indeg_exc, N, sums);
+    k_scan_carry<<<1, 256, 0, s>>>(sums, scan_blocks);
+    k_scan_write<<<scan_blocks, 256, 0, s>>>(indeg_exc, N, sums, net->rin_off);
+    int64_t n_rin = 0;
+    SNN_CUDA(cudaMemcpyAsync(&n_rin, net->rin_off + N, 8, cudaMemcpyDeviceToHost, s));
+    SNN_CUDA(cudaStreamSynchronize(s));
+    net->n_rin = n_rin;
+    SNN_TRY(dalloc_t(net, (size_t)std::max<int64_t>(n_rin, 1), &net->rin));
+    dn.rin = net->rin;
+    k_fill_reverse<<<g, 256, 0, s>>>(dn, cursor, net->rin);
+    SNN_CUDA(cudaGetLastError());
+    SNN_CUDA(cudaStreamSynchronize(s));
+    dfree(net, indeg_exc);
+    dfree(net, indeg_inh);
+    dfree(net, cursor);
+    dfree(net, mx);
+    dfree(net, sums);
+
+    std::vector<int32_t> lut;
+    SNN_TRY(build_luts(&net->cfg, lut));
+    SNN_CUDA(cudaMemcpyAsync(net->lut, lut.data(), lut.size() * 4, cudaMemcpyHostToDevice, s));
+    k_init_state<<<g, 256, 0, s>>>(dn);
+    DevCounters hc{};
+    hc.raster_first_drop_t = 0x7fffffff;
+    hc.t_slot[0] = 0;
+    hc.t_slot[1] = 0;
+    SNN_CUDA(cudaMemcpyAsync(net->ctr, &hc, sizeof hc, cudaMemcpyHostToDevice, s));
+    SNN_CUDA(cudaMemsetAsync(dn.ring_cnt, 0, (size_t)2 * net->cfg.max_delay_ms * 4, s));
+    if (dn.raster_step_off) SNN_CUDA(cudaMemsetAsync(dn.raster_step_off, 0, 8, s));
+    SNN_CUDA(cudaGetLastError());
+    SNN_CUDA(cudaStreamSynchronize(s));
+    return SNN_OK;
+}
+
+int start_net(const snn_config *cfg, void *cuda_stream, size_t budget, snn_net **out, snn_net **made)
+{
+    SNN_TRY(check_config(cfg));
+    if (!out) { set_error("out is NULL"); return SNN_EINVAL; }
+    snn_net *net = new snn_net();
+    *made = net;
+    net->cfg = *cfg;
+    net->budget = budget;
+    net->alloc = g_alloc;
+    net->release = g_release;
+    net->alloc_ctx = g_alloc_ctx;
+    net->N = cfg->grid_x * cfg->grid_y * cfg->neurons_per_col;
+    net->launch.deliver_block = 256;
+    net->launch.deliver_blocks_per_sm = 8;
+    net->launch.neuron_block = 256;
+    net->launch.ltp_block = 256;
+    net->launch.ltp_blocks_per_sm = 8;
+    net->launch.deriv_block = 256;
+    net->launch.graph_steps = 50;
+    (void)cuda_stream;
+    return SNN_OK;
+}
+
+// device, SM count and stream (after every host-side check has passed)
+int cuda_init(snn_net *net, void *cuda_stream)
+{
+    SNN_CUDA(cudaGetDevice(&net->device));
+    SNN_CUDA(cudaDeviceGetAttribute(&net->sm_count, cudaDevAttrMultiProcessorCount, net->device));
+    if (cuda_stream) {
+        net->stream = (cudaStream_t)cuda_stream;
+    } else {
+        SNN_CUDA(cudaStreamCreateWithFlags(&net->stream, cudaStreamNonBlocking));
+        net->own_stream = true;
+    }
+    return SNN_OK;
+}
+
+int ensure_raster_steps(snn_net *net, int64_t needed)
+{
+    if (!net->dn.raster_step_off || needed <= net->raster_steps_cap) return SNN_OK;
+    int64_t cap = net->raster_steps_cap;
+    while (cap < needed) cap *= 2;
+    int64_t *p = nullptr;
+    SNN_TRY(dalloc_t(net, (size_t)cap, &p));
+    SNN_CUDA(cudaMemcpyAsync(p, net->dn.raster_step_off, (size_t)net->raster_steps_cap * 8,
+                             cudaMemcpyDeviceToDevice, net->stream));
+    SNN_CUDA(cudaStreamSynchronize(net->stream));
+    dfree(net, net->dn.raster_step_off);
+    net->dn.raster_step_off = p;
+    net->raster_steps_cap = cap;
+    drop_graphs(net);
+    return SNN_OK;
+}
+
+cudaEvent_t next_event(snn_net *net, int kind)
+{
+    if (net->ev_used == net->ev_pool.size()) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        net->ev_pool.push_back(e);
+        net->ev_kind.push_back(0);
+    }
+    net->ev_kind[net->ev_used] = kind;
+    return net->ev_pool[net->ev_used++];
+}
+
+void launch_step(snn_net *net, int32_t t, bool deriv)
+{
+    const DevNet &dn = net->dn;
+    cudaStream_t s = net->stream;
+    const int *t_now = &net->ctr->t_slot[t & 1];
+    int *t_next = &net->ctr->t_slot[(t & 1) ^ 1];
+    const snn_launch &L = net->launch;
+    const bool prof = net->profile;
+    cudaEvent_t e0, e1;
+    const int nb_neuron = (int)((net->N + L.neuron_block * kNeuronsPerThread - 1) /
+                                (L.neuron_block * kNeuronsPerThread));
+    // S1
+    if (prof) { e0 = next_event(net, 0); cudaEventRecord(e0, s); }
+    k_deliver<<<grid_for(net, L.deliver_blocks_per_sm), L.deliver_block, 0, s>>>(dn, t_now);
+    if (prof) { e1 = next_event(net, 0); cudaEventRecord(e1, s); }
+    // S2 + S3
+    if (prof) { e0 = next_event(net, 1); cudaEventRecord(e0, s); }
+    k_neuron<<<nb_neuron, L.neuron_block, 0, s>>>(dn, t_now);
+    if (prof) { e1 = next_event(net, 1); cudaEventRecord(e1, s); }
+    // S4
+    if (prof) { e0 = next_event(net, 2); cudaEventRecord(e0, s); }
+    k_ltp<<<grid_for(net, L.ltp_blocks_per_sm), L.ltp_block, 0, s>>>(dn, t_now, t_next);
+    if (prof) { e1 = next_event(net, 2); cudaEventRecord(e1, s); }
+    // S5
+    if (deriv) {
+        const uint32_t C = dn.C;
+        const int64_t per_col = (int64_t)dn.ne * (dn.uniform_m ? dn.uniform_m : 1);
+        uint32_t gx = (uint32_t)std::min<int64_t>(1024, std::max<int64_t>(1, per_col / ((int64_t)L.deriv_block * 4)));
+        if (!dn.uniform_m) gx = (uint32_t)std::min<int64_t>(1024, std::max<int64_t>(1, (net->S / std::max(1u, C)) / L.deriv_block + 1));
+        if (prof) { e0 = next_event(net, 3); cudaEventRecord(e0, s); }
+        k_deriv<<<dim3(gx, C), L.deriv_block, 0, s>>>(dn, 0);
+        if (prof) { e1 = next_event(net, 3); cudaEventRecord(e1, s); }
+    }
+}
+
+uint32_t effective_graph_len(const snn_net *net)
+{
+    uint32_t L = net->launch.graph_steps;
+    if (net->profile || L < 2) return 0;
+    const uint32_t P = net->cfg.deriv_period_ms;
+    if (P == 0) return L & ~1u;
+    for (uint32_t l = std::min(L, P) & ~1u; l >= 2; l -= 2)
+        if (P % l == 0) return l;
+    return 0;
+}
+
+int build_graph(snn_net *net, int variant, uint32_t L)
+{
+    cudaGraph_t g = nullptr;
+    SNN_CUDA(cudaStreamBeginCapture(net->stream, cudaStreamCaptureModeThreadLocal));
+    for (uint32_t k = 0; k < L; ++k) launch_step(net, (int32_t)k, variant && k + 1 == L);
+    cudaError_t e = cudaStreamEndCapture(net->stream, &g);
+    if (e != cudaSuccess) {
+        set_error("graph capture failed: %s", cudaGetErrorString(e));
+        return SNN_ECUDA;
+    }
+    e = cudaGraphInstantiate(&net->graph[variant], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        net->graph[variant] = nullptr;
+        set_error("graph instantiate failed: %s", cudaGetErrorString(e));
+        return SNN_ECUDA;
+    }
+    return SNN_OK;
+}
+
+int read_counters_raw(snn_net *net, DevCounters *hc)
+{
+    SNN_CUDA(cudaMemcpyAsync(hc, net->ctr, sizeof *hc, cudaMemcpyDeviceToHost, net->stream));
+    SNN_CUDA(cudaStreamSynchronize(net->stream));
+    return SNN_OK;
+}
+
+int finish_run(snn_net *net)
+{
+    SNN_CUDA(cudaStreamSynchronize(net->stream));
+    SNN_CUDA(cudaGetLastError());
+    if (net->profile && net->ev_used) {
+        for (size_t i = 0; i + 1 < net->ev_used; i += 2) {
+            float ms = 0.f;
+            SNN_CUDA(cudaEventElapsedTime(&ms, net->ev_pool[i], net->ev_pool[i + 1]));
+            net->prof_ms[net->ev_kind[i]] += ms;
+            net->prof_n[net->ev_kind[i]] += 1;
+        }
+        net->ev_used = 0;
+    }
+    DevCounters hc{};
+    SNN_TRY(read_counters_raw(net, &hc));
+    if (hc.error) {
+        set_error("device error word %d", hc.error);
+        return hc.error == SNN_ETIMEOUT ? SNN_ETIMEOUT : SNN_ECUDA;
+    }
+    return SNN_OK;
+}
+
+int run_steps(snn_net *net, uint32_t n_ms)
+{
+    if ((int64_t)net->t + n_ms > 0x7fff0000ll) { set_error("time limit reached"); return SNN_ESTATE; }
+    SNN_TRY(ensure_raster_steps(net, (int64_t)net->t + n_ms + 2 - net->dn.raster_t0));
+    const uint32_t P = net->cfg.deriv_period_ms;
+    const uint32_t L = effective_graph_len(net);
+    if (L != net->graph_len) {
+        drop_graphs(net);
+        net->graph_len = L;
+    }
+    uint32_t left = n_ms;
+    while (left > 0) {
+        const int32_t t = net->t;
+        if (L >= 2 && (uint32_t)t % L == 0 && left >= L) {
+            const int variant = (P && ((uint32_t)t + L) % P == 0) ? 1 : 0;
+            if (net->graphs_dirty) {
+                for (int i = 0; i < 2; ++i)
+                    if (net->graph[i]) { cudaGraphExecDestroy(net->graph[i]); net->graph[i] = nullptr; }
+                net->graphs_dirty = false;
+            }
+            if (!net->graph[variant]) SNN_TRY(build_graph(net, variant, L));
+            SNN_CUDA(cudaGraphLaunch(net->graph[variant], net->stream));
+            net->t += (int32_t)L;
+            left -= L;
+        } else {
+            launch_step(net, t, P && ((uint32_t)t + 1) % P == 0);
+            SNN_CUDA(cudaGetLastError());
+            net->t += 1;
+            left -= 1;
+        }
+    }
+    return finish_run(net);
+}
+
+int set_stimulus_impl(snn_net *net, const snn_stimulus *ev, size_t n)
+{
+    DevNet &dn = net->dn;
+    if (n == 0) {
+        dn.stim_t0 = dn.stim_t1 = 0;
+        drop_graphs(net);
+        return SNN_OK;
+    }
+    if (!ev) { set_error("events is NULL"); return SNN_EINVAL; }
+    std::vector<snn_stimulus> e;
+    e.reserve(n);
+    for (size_t i = 0; i < n; ++i) {
+        if (ev[i].gid < 0 || (uint32_t)ev[i].gid >= net->N) {
+            set_error("stimulus %zu: gid %d out of range", i, ev[i].gid);
+            return SNN_EINVAL;
+        }
+        if (ev[i].t >= net->t) e.push_back(ev[i]);
+    }
+    if (e.empty()) {
+        dn.stim_t0 = dn.stim_t1 = 0;
+        drop_graphs(net);
+        return SNN_OK;
+    }
+    std::stable_sort(e.begin(), e.end(), [](const snn_stimulus &a, const snn_stimulus &b) { return a.t < b.t; });
+    const int32_t t0 = e.front().t, t1 = e.back().t + 1;
+    std::vector<int32_t> gid(e.size()), q(e.size());
+    std::vector<int64_t> off((size_t)(t1 - t0) + 1, 0);
+    for (size_t i = 0; i < e.size(); ++i) {
+        gid[i] = e[i].gid;
+        q[i] = e[i].q16;
+        off[(size_t)(e[i].t - t0) + 1]++;
+    }
+    for (size_t k = 1; k < off.size(); ++k) off[k] += off[k - 1];
+    if (e.size() > net->stim_cap) {
+        dfree(net, (void *)dn.stim_gid);
+        dfree(net, (void *)dn.stim_q16);
+        dn.stim_gid = dn.stim_q16 = nullptr;
+        int32_t *a = nullptr, *b = nullptr;
+        SNN_TRY(dalloc_t(net, e.size(), &a));
+        SNN_TRY(dalloc_t(net, e.size(), &b));
+        dn.stim_gid = a;
+        dn.stim_q16 = b;
+        net->stim_cap = e.size();
+    }
+    if ((int64_t)off.size() > net->stim_off_cap) {
+        dfree(net, (void *)dn.stim_off);
+        dn.stim_off = nullptr;
+        int64_t *o = nullptr;
+        SNN_TRY(dalloc_t(net, off.size(), &o));
+        dn.stim_off = o;
+        net->stim_off_cap = (int64_t)off.size();
+    }
+    SNN_CUDA(cudaMemcpyAsync((void *)dn.stim_gid, gid.data(), gid.size() * 4, cudaMemcpyHostToDevice, net->stream));
+    SNN_CUDA(cudaMemcpyAsync((void *)dn.stim_q16, q.data(), q.size() * 4, cudaMemcpyHostToDevice, net->stream));
+    SNN_CUDA(cudaMemcpyAsync((void *)dn.stim_off, off.data(), off.size() * 8, cudaMemcpyHostToDevice, net->stream));
+    SNN_CUDA(cudaStreamSynchronize(net->stream));
+    dn.stim_t0 = t0;
+    dn.stim_t1 = t1;
+    drop_graphs(net);
+    return SNN_OK;
+}
+
+int raster_window(snn_net *net, int32_t t0, int32_t t1, std::vector<snn_spike> &out, bool &truncated)
+{
+    out.clear();
+    truncated = false;
+    DevNet &dn = net->dn;
+    if (!dn.raster_gid) { set_error("the net keeps no raster (raster_capacity = 0)"); return SNN_ESTATE; }
+    const int32_t lo = std::max(t0, dn.raster_t0), hi = std::min(t1, net->t);
+    if (t0 < dn.raster_t0) truncated = true;
+    if (hi <= lo) return SNN_OK;
+    std::vector<int64_t> off((size_t)(hi - lo) + 1);
+    SNN_CUDA(cudaMemcpyAsync(off.data(), dn.raster_step_off + (lo - dn.raster_t0), off.size() * 8,
+                             cudaMemcpyDeviceToHost, net->stream));
+    SNN_CUDA(cudaStreamSynchronize(net->stream));
+    const int64_t a = off.front(), b = off.back();
+    std::vector<int32_t> gid((size_t)(b - a));
+    if (b > a) {
+        SNN_CUDA(cudaMemcpyAsync(gid.data(), dn.raster_gid + a, (size_t)(b - a) * 4, cudaMemcpyDeviceToHost,
+                                 net->stream));
+        SNN_CUDA(cudaStreamSynchronize(net->stream));
+    }
+    out.resize(gid.size());
+    for (int32_t t = lo; t < hi; ++t) {
+        const int64_t s0 = off[(size_t)(t - lo)] - a, s1 = off[(size_t)(t - lo) + 1] - a;
+        std::sort(gid.begin() + s0, gid.begin() + s1);
+        for (int64_t k = s0; k < s1; ++k) out[(size_t)k] = snn_spike{t, gid[(size_t)k]};
+    }
+    DevCounters hc{};
+    SNN_TRY(read_counters_raw(net, &hc));
+    if (hc.raster_dropped && hi > hc.raster_first_drop_t) truncated = true;
+    return SNN_OK;
+}
+
+int raster_reset_impl(snn_net *net)
+{
+    DevNet &dn = net->dn;
+    if (!dn.raster_gid) return SNN_OK;
+    DevCounters hc{};
+    SNN_TRY(read_counters_raw(net, &hc));
+    hc.raster_total = 0;
+    hc.raster_dropped = 0;
+    hc.raster_first_drop_t = 0x7fffffff;
+    SNN_CUDA(cudaMemcpyAsync(net->ctr, &hc, sizeof hc, cudaMemcpyHostToDevice, net->stream));
+    SNN_CUDA(cudaMemsetAsync(dn.raster_step_off, 0, 8, net->stream));
+    SNN_CUDA(cudaStreamSynchronize(net->stream));
+    dn.raster_t0 = net->t;
+    drop_graphs(net);
+    return SNN_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+const char *snn_strerror(int code)
+{
+    switch (code) {
+    case SNN_OK: return "ok";
+    case SNN_EINVAL: return "invalid argument or configuration";
+    case SNN_ENOMEM: return "device memory budget exceeded or allocation failed";
+    case SNN_ECUDA: return "CUDA error";
+    case SNN_EOVERFLOW: return "Q16 current bound cannot be guaranteed";
+    case SNN_ETIMEOUT: return "bounded device wait gave up";
+    case SNN_ETRUNC: return "output truncated";
+    case SNN_ESTATE: return "call does not fit the state of the handle";
+    default: return "unknown error";
+    }
+}
+
+const char *snn_last_error(void) { return g_last_error.c_str(); }
+
+void snn_set_allocator(void *(*alloc)(size_t, void *, void *), void (*release)(void *, void *), void *ctx)
+{
+    g_alloc = alloc;
+    g_release = release;
+    g_alloc_ctx = ctx;
+}
+
+void snn_free(snn_net *net)
+{
+    if (!net) return;
+    if (net->stream) cudaStreamSynchronize(net->stream);
+    drop_graphs(net);
+    for (cudaEvent_t e : net->ev_pool) cudaEventDestroy(e);
+    while (!net->blocks.empty()) dfree(net, net->blocks.back().p);
+    if (net->own_stream && net->stream) cudaStreamDestroy(net->stream);
+    delete net;
+}
+
+int snn_build_network(const snn_config *cfg, void *cuda_stream, size_t hbm_budget_bytes, snn_net **out)
+{
+    snn_net *net = nullptr;
+    int r = start_net(cfg, cuda_stream, hbm_budget_bytes, out, &net);
+    auto fail = [&](int code) { snn_free(net); if (out) *out = nullptr; return code; };
+    if (r != SNN_OK) return fail(r);
+    const snn_config &c = net->cfg;
+    net->S = (int64_t)net->N * c.fanout;
+    const int64_t n_rin_est = (int64_t)c.grid_x * c.grid_y * c.exc_per_col * c.fanout;
+    const size_t need = footprint(&c, net->N, net->S, n_rin_est, false) + (size_t)c.raster_capacity * 4 + (1 << 17);
+    if (hbm_budget_bytes && need > hbm_budget_bytes) {
+        set_error("network needs about %zu bytes, budget is %zu", need, hbm_budget_bytes);
+        return fail(SNN_ENOMEM);
+    }
+    if ((r = cuda_init(net, cuda_stream)) != SNN_OK) return fail(r);
+    if ((r = alloc_common(net)) != SNN_OK) return fail(r);
+    net->dn.uniform_m = c.fanout;
+    net->wrange = WeightRange{c.w_exc0_q16, c.w_exc0_q16, c.w_inh0_q16, c.w_inh0_q16};
+    GenParams &g = net->gen;
+    g.npc = c.neurons_per_col;
+    g.ne = c.exc_per_col;
+    g.m = c.fanout;
+    g.D = c.max_delay_ms;
+    g.gx = c.grid_x;
+    g.gy = c.grid_y;
+    uint32_t acc = 0;
+    for (int k = 0; k < 4; ++k) {
+        acc += c.pct_ring[k];
+        g.ring_end[k] = (uint32_t)(((uint64_t)c.fanout * acc) / 100u);
+    }
+    g.seed_lo = net->dn.seed_lo;
+    g.seed_hi = net->dn.seed_hi;
+    g.w_exc0 = c.w_exc0_q16;
+    g.w_inh0 = c.w_inh0_q16;
+    const int gr = grid_for(net, 16);
+    k_fill_row_off<<<gr, 256, 0, net->stream>>>(net->row_off, net->N, c.fanout);
+    k_gen_rows<<<gr, 256, 0, net->stream>>>(g, net->N, net->doff, net->tgt, net->w, net->sd);
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(net->stream) != cudaSuccess) {
+        set_error("network generation failed: %s", cudaGetErrorString(cudaGetLastError()));
+        return fail(SNN_ECUDA);
+    }
+    if ((r = finish_build(net)) != SNN_OK) return fail(r);
+    *out = net;
+    return SNN_OK;
+}
+
+int snn_build_network_explicit(const snn_config *cfg, const int64_t *host_row_off, const int32_t *host_tgt,
+                               const uint8_t *host_delay, const int32_t *host_w, void *cuda_stream,
+                               size_t hbm_budget_bytes, snn_net **out)
+{
+    snn_net *net = nullptr;
+    int r = start_net(cfg, cuda_stream, hbm_budget_bytes, out, &net);
+    auto fail = [&](int code) { snn_free(net); if (out) *out = nullptr; return code; };
+    if (r != SNN_OK) return fail(r);
+    if (!host_row_off) { set_error("row offsets are NULL"); return fail(SNN_EINVAL); }
+    const uint32_t N = net->N;
+    const uint32_t D = net->cfg.max_delay_ms;
+    if (host_row_off[0] != 0) { set_error("row_off[0] must be 0"); return fail(SNN_EINVAL); }
+    for (uint32_t p = 0; p < N; ++p) {
+        const int64_t len = host_row_off[p + 1] - host_row_off[p];
+        if (len < 0 || len > 65535) { set_error("row %u has %lld synapses (0..65535)", p, (long long)len); return fail(SNN_EINVAL); }
+    }
+    const int64_t S = host_row_off[N];
+    if (S > 0 && (!host_tgt || !host_delay || !host_w)) { set_error("synapse arrays are NULL"); return fail(SNN_EINVAL); }
+    for (int64_t k = 0; k < S; ++k) {
+        if (host_tgt[k] < 0 || (uint32_t)host_tgt[k] >= N || host_delay[k] < 1 || host_delay[k] > D) {
+            set_error("synapse %lld: target or delay out of range", (long long)k);
+            return fail(SNN_EINVAL);
+        }
+    }
+    net->explicit_net = true;
+    net->S = S;
+    int64_t n_exc = 0;
+    net->wrange = WeightRange{0, 0, 0, 0};
+    for (uint32_t p = 0; p < N; ++p) {
+        const bool exc = (p % net->cfg.neurons_per_col) < net->cfg.exc_per_col;
+        if (exc) n_exc += host_row_off[p + 1] - host_row_off[p];
+        for (int64_t k = host_row_off[p]; k < host_row_off[p + 1]; ++k) {
+            WeightRange &r = net->wrange;
+            if (exc) { r.exc_min = std::min(r.exc_min, host_w[k]); r.exc_max = std::max(r.exc_max, host_w[k]); }
+            else { r.inh_min = std::min(r.inh_min, host_w[k]); r.inh_max = std::max(r.inh_max, host_w[k]); }
+        }
+    }
+    const size_t need = footprint(&net->cfg, N, S, n_exc, true) + (size_t)net->cfg.raster_capacity * 4 + (1 << 17);
+    if (hbm_budget_bytes && need > hbm_budget_bytes) {
+        set_error("network needs about %zu bytes, budget is %zu", need, hbm_budget_bytes);
+        return fail(SNN_ENOMEM);
+    }
+    if ((r = cuda_init(net, cuda_stream)) != SNN_OK) return fail(r);
+    if ((r = alloc_common(net)) != SNN_OK) return fail(r);
+    if ((r = dalloc_t(net, (size_t)std::max<int64_t>(S, 1), &net->canon_delay)) != SNN_OK) return fail(r);
+    net->dn.uniform_m = 0;
+    // stable counting sort of every row by delay
+    std::vector<int32_t> tg((size_t)S), ww((size_t)S);
+    std::vector<uint16_t> doff((size_t)N * kDoffStride, 0);
+    for (uint32_t p = 0; p < N; ++p) {
+        const int64_t lo = host_row_off[p], hi = host_row_off[p + 1];
+        uint32_t cnt[kDoffStride] = {0};
+        for (int64_t k = lo; k < hi; ++k) cnt[host_delay[k]]++;
+        uint16_t *o = &doff[(size_t)p * kDoffStride];
+        uint32_t accd = 0;
+        uint32_t start[kDoffStride] = {0};
+        for (uint32_t d = 0; d <= D; ++d) {
+            start[d] = accd;
+            accd += cnt[d];
+            o[d] = (uint16_t)accd;
+        }
+        for (int64_t k = lo; k < hi; ++k) {
+            const int64_t pos = lo + start[host_delay[k]]++;
+            tg[(size_t)pos] = host_tgt[k];
+            ww[(size_t)pos] = host_w[k];
+        }
+    }
+    cudaStream_t s = net->stream;
+    if (cudaMemcpyAsync(net->row_off, host_row_off, ((size_t)N + 1) * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(net->doff, doff.data(), doff.size() * 2, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        (S > 0 && (cudaMemcpyAsync(net->tgt, tg.data(), (size_t)S * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+                   cudaMemcpyAsync(net->w, ww.data(), (size_t)S * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+                   cudaMemsetAsync(net->sd, 0, (size_t)S * 4, s) != cudaSuccess ||
+                   cudaMemcpyAsync(net->canon_delay, host_delay, (size_t)S, cudaMemcpyHostToDevice, s) != cudaSuccess)) ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        set_error("upload failed: %s", cudaGetErrorString(cudaGetLastError()));
+        return fail(SNN_ECUDA);
+    }
+    if ((r = finish_build(net)) != SNN_OK) return fail(r);
+    *out = net;
+    return SNN_OK;
+}
+
+int snn_set_stimulus(snn_net *net, const snn_stimulus *host_events, size_t n)
+{
+    if (!net) { set_error("net is NULL"); return SNN_EINVAL; }
+    return set_stimulus_impl(net, host_events, n);
+}
+
+int snn_set_thalamic(snn_net *net, int on)
+{
+    if (!net) { set_error("net is NULL"); return SNN_EINVAL; }
+    net->dn.thal_per_col = on ? net->cfg.thal_per_col_per_ms : 0u;
+    drop_graphs(net);
+    return SNN_OK;
+}
+
+int snn_set_launch(snn_net *net, const snn_launch *launch)
+{
+    if (!net || !launch) { set_error("NULL argument"); return SNN_EINVAL; }
+    snn_launch L = net->launch;
+    auto pick = [](uint32_t v, uint32_t cur) { return v ? v : cur; };
+    L.deliver_block = pick(launch->deliver_block, L.deliver_block);
+    L.deliver_blocks_per_sm = pick(launch->deliver_blocks_per_sm, L.deliver_blocks_per_sm);
+    L.neuron_block = pick(launch->neuron_block, L.neuron_block);
+    L.ltp_block = pick(launch->ltp_block, L.ltp_block);
+    L.ltp_blocks_per_sm = pick(launch->ltp_blocks_per_sm, L.ltp_blocks_per_sm);
+    L.deriv_block = pick(launch->deriv_block, L.deriv_block);
+    L.graph_steps = pick(launch->graph_steps, L.graph_steps);
+    for (uint32_t b : {L.deliver_block, L.neuron_block, L.ltp_block, L.deriv_block}) {
+        if (b < 32 || b > 1024 || b % 32) { set_error("block sizes must be multiples of 32 in 32..1024"); return SNN_EINVAL; }
+    }
+    if (L.deliver_blocks_per_sm > 64 || L.ltp_blocks_per_sm > 64) { set_error("blocks per SM must be <= 64"); return SNN_EINVAL; }
+    net->launch = L;
+    drop_graphs(net);
+    return SNN_OK;
+}
+
+int snn_get_launch(const snn_net *net, snn_launch *launch)
+{
+    if (!net || !launch) { set_error("NULL argument"); return SNN_EINVAL; }
+    *launch = net->launch;
+    return SNN_OK;
+}
+
+int snn_step(snn_net *net)
+{
+    if (!net) { set_error("net is NULL"); return SNN_EINVAL; }
+    return run_steps(net, 1);
+}
+
+int snn_run(snn_net *net, uint32_t n_ms)
+{
+    if (!net) { set_error("net is NULL"); return SNN_EINVAL; }
+    if (n_ms == 0) return SNN_OK;
+    return run_steps(net, n_ms);
+}
+
+int snn_run_host(snn_net *net, uint32_t n_ms, const snn_stimulus *host_stimulus, size_t n_stim,
+                 snn_spike *host_spikes, size_t cap, size_t *n_out)
+{
+    if (!net) { set_error("net is NULL"); return SNN_EINVAL; }
+    const int32_t t0 = net->t;
+    SNN_TRY(set_stimulus_impl(net, host_stimulus, host_stimulus ? n_stim : 0));
+    if (!host_spikes) {
+        DevCounters a{}, b{};
+        SNN_TRY(read_counters_raw(net, &a));
+        SNN_TRY(run_steps(net, n_ms));
+        SNN_TRY(read_counters_raw(net, &b));
+        if (n_out) *n_out = (size_t)(b.spikes - a.spikes);
+        return SNN_OK;
+    }
+    if (!net->dn.raster_gid) { set_error("snn_run_host needs raster_capacity > 0"); return SNN_ESTATE; }
+    if (net->dn.raster_t0 != t0) SNN_TRY(raster_reset_impl(net));
+    SNN_TRY(run_steps(net, n_ms));
+    std::vector<snn_spike> out;
+    bool trunc = false;
+    SNN_TRY(raster_window(net, t0, t0 + (int32_t)n_ms, out, trunc));
+    if (n_out) *n_out = out.size();
+    const size_t k = std::min(cap, out.size());
+    if (k && host_spikes) std::memcpy(host_spikes, out.data(), k * sizeof(snn_spike));
+    SNN_TRY(raster_reset_impl(net));
+    if (trunc || out.size() > cap) { set_error("raster window truncated"); return SNN_ETRUNC; }
+    return SNN_OK;
+}
+
+int snn_reset(snn_net *net)
+{
+    if (!net) { set_error("net is NULL"); return SNN_EINVAL; }
+    if (net->explicit_net) { set_error("explicit nets keep no copy of their initial weights"); return SNN_ESTATE; }
+    cudaStream_t s = net->stream;
+    const int g = grid_for(net, 8);
+    k_reset_weights<<<g, 256, 0, s>>>(net->dn, net->gen.w_exc0, net->gen.w_inh0);
+    k_init_state<<<g, 256, 0, s>>>(net->dn);
+    DevCounters hc{};
+    hc.raster_first_drop_t = 0x7fffffff;
+    SNN_CUDA(cudaMemcpyAsync(net->ctr, &hc, sizeof hc, cudaMemcpyHostToDevice, s));
+    SNN_CUDA(cudaMemsetAsync(net->dn.ring_cnt, 0, (size_t)2 * net->cfg.max_delay_ms * 4, s));
+    if (net->dn.raster_step_off) SNN_CUDA(cudaMemsetAsync(net->dn.raster_step_off, 0, 8, s));
+    SNN_CUDA(cudaGetLastError());
+    SNN_CUDA(cudaStreamSynchronize(s));
+    net->t = 0;
+    net->dn.raster_t0 = 0;
+    net->dn.stim_t0 = net->dn.stim_t1 = 0;
+    drop_graphs(net);
+    return SNN_OK;
+}
+
+int snn_thalamic_events(const snn_config *cfg, int32_t t0, uint32_t n_ms, snn_stimulus *host_events, size_t cap,
+                        size_t *n_out)
+{
+    SNN_TRY(check_config(cfg));
+    if (t0 < 0) { set_error("t0 must be >= 0"); return SNN_EINVAL; }
+    const uint32_t C = cfg->grid_x * cfg->grid_y, K = cfg->thal_per_col_per_ms, npc = cfg->neurons_per_col;
+    const size_t total = (size_t)n_ms * C * K;
+    if (n_out) *n_out = total;
+    if (total > cap || (!host_events && total)) { set_error("need %zu events", total); return SNN_ETRUNC; }
+    const uint32_t k0 = (uint32_t)(cfg->seed & 0xffffffffu), k1 = (uint32_t)(cfg->seed >> 32);
+    size_t i = 0;
+    for (uint32_t s = 0; s < n_ms; ++s) {
+        const uint32_t t = (uint32_t)t0 + s;
+        for (uint32_t col = 0; col < C; ++col)
+            for (uint32_t k = 0; k < K; ++k) {
+                const uint4 r = philox10(make_uint4(t, col, 1u, k), k0, k1);
+                host_events[i++] = snn_stimulus{(int32_t)t, (int32_t)(col * npc + draw_below(r.x, npc)),
+                                                cfg->thal_amp_q16};
+            }
+    }
+    return SNN_OK;
+}
+
+int snn_read_raster(snn_net *net, int32_t t0, int32_t t1, snn_spike *host_buf, size_t cap, size_t *n_out)
+{
+    if (!net) { set_error("net is NULL"); return SNN_EINVAL; }
+    std::vector<snn_spike> out;
+    bool trunc = false;
+    SNN_TRY(raster_window(net, t0, t1, out, trunc));
+    if (n_out) *n_out = out.size();
+    const size_t k = std::min(cap, out.size());
+    if (k && host_buf) std::memcpy(host_buf, out.data(), k * sizeof(snn_spike));
+    if (trunc || out.size() > cap) { set_error("raster window truncated"); return SNN_ETRUNC; }
+    return SNN_OK;
+}
+
+int snn_raster_reset(snn_net *net)
+{
+    if (!net) { set_error("net is NULL"); return SNN_EINVAL; }
+    return raster_reset_impl(net);
+}
+
+int snn_read_synapses(snn_net *net, uint32_t first, uint32_t count, int32_t *host_tgt, uint8_t *host_delay,
+                      int32_t *host_w, int32_t *host_sd, size_t cap, size_t *n_out)
+{
+    if (!net) { set_error("net is NULL"); return SNN_EINVAL; }
+    if ((uint64_t)first + count > net->N) { set_error("row range out of bounds"); return SNN_EINVAL; }
+    std::vector<int64_t> ro(2);
+    SNN_CUDA(cudaMemcpyAsync(&ro[0], net->row_off + first, 8, cudaMemcpyDeviceToHost, net->stream));
+    SNN_CUDA(cudaMemcpyAsync(&ro[1], net->row_off + first + count, 8, cudaMemcpyDeviceToHost, net->stream));
+    SNN_CUDA(cudaStreamSynchronize(net->stream));
+    const int64_t total = ro[1] - ro[0];
+    if (n_out) *n_out = (size_t)total;
+    if ((size_t)total > cap) { set_error("need %lld entries", (long long)total); return SNN_ETRUNC; }
+    if (total == 0) return SNN_OK;
+    // chunks of rows of at most ~64 M synapses through device scratch
+    const int64_t chunk_syn = 64ll << 20;
+    uint32_t r0 = first;
+    std::vector<int64_t> offs;
+    while (r0 < first + count) {
+        // find r1 with row_off[r1] - row_off[r0] <= chunk_syn (rows hold <= 65535)
+        uint32_t r1 = std::min<uint32_t>(first + count, r0 + (uint32_t)std::max<int64_t>(1, chunk_syn / 65536));
+        int64_t a = 0, b = 0;
+        SNN_CUDA(cudaMemcpyAsync(&a, net->row_off + r0, 8, cudaMemcpyDeviceToHost, net->stream));
+        SNN_CUDA(cudaMemcpyAsync(&b, net->row_off + r1, 8, cudaMemcpyDeviceToHost, net->stream));
+        SNN_CUDA(cudaStreamSynchronize(net->stream));
+        const int64_t n = b - a;
+        if (n > 0) {
+            int32_t *dt = nullptr, *dw = nullptr, *ds = nullptr;
+            uint8_t *dd = nullptr;
+            if (host_tgt) SNN_TRY(dalloc_t(net, (size_t)n, &dt));
+            if (host_delay) SNN_TRY(dalloc_t(net, (size_t)n, &dd));
+            if (host_w) SNN_TRY(dalloc_t(net, (size_t)n, &dw));
+            if (host_sd) SNN_TRY(dalloc_t(net, (size_t)n, &ds));
+            k_read_rows<<<grid_for(net, 8), 128, 0, net->stream>>>(net->dn, net->gen, net->canon_delay, r0, r1 - r0,
+                                                                   a, dt, dd, dw, ds);
+            SNN_CUDA(cudaGetLastError());
+            const size_t o = (size_t)(a - ro[0]);
+            if (dt) SNN_CUDA(cudaMemcpyAsync(host_tgt + o, dt, (size_t)n * 4, cudaMemcpyDeviceToHost, net->stream));
+            if (dd) SNN_CUDA(cudaMemcpyAsync(host_delay + o, dd, (size_t)n, cudaMemcpyDeviceToHost, net->stream));
+            if (dw) SNN_CUDA(cudaMemcpyAsync(host_w + o, dw, (size_t)n * 4, cudaMemcpyDeviceToHost, net->stream));
+            if (ds) SNN_CUDA(cudaMemcpyAsync(host_sd + o, ds, (size_t)n * 4, cudaMemcpyDeviceToHost, net->stream));
+            SNN_CUDA(cudaStreamSynchronize(net->stream));
+            dfree(net, dt);
+            dfree(net, dd);
+            dfree(net, dw);
+            dfree(net, ds);
+        }
+        r0 = r1;
+    }
+    return SNN_OK;
+}
+
+int snn_read_weights(snn_net *net, int32_t *host_w, int32_t *host_sd, size_t cap, size_t *n_out)
+{
+    if (!net) { set_error("net is NULL"); return SNN_EINVAL; }
+    return snn_read_synapses(net, 0, net->N, nullptr, nullptr, host_w, host_sd, cap, n_out);
+}
+
+int snn_read_neurons(snn_net *net, uint32_t first, uint32_t count, float *host_v, float *host_u)
+{
+    if (!net) { set_error("net is NULL"); return SNN_EINVAL; }
+    if ((uint64_t)first + count > net->N) { set_error("neuron range out of bounds"); return SNN_EINVAL; }
+    if (host_v) SNN_CUDA(cudaMemcpyAsync(host_v, net->dn.v + first, (size_t)count * 4, cudaMemcpyDeviceToHost, net->stream));
+    if (host_u) SNN_CUDA(cudaMemcpyAsync(host_u, net->dn.u + first, (size_t)count * 4, cudaMemcpyDeviceToHost, net->stream));
+    SNN_CUDA(cudaStreamSynchronize(net->stream));
+    return SNN_OK;
+}
+
+int snn_read_counters(snn_net *net, snn_counters *out)
+{
+    if (!net || !out) { set_error("NULL argument"); return SNN_EINVAL; }
+    DevCounters hc{};
+    SNN_TRY(read_counters_raw(net, &hc));
+    out->t = net->t;
+    out->spikes = (int64_t)hc.spikes;
+    out->e_all = (int64_t)hc.e_all;
+    out->e_exc = (int64_t)hc.e_exc;
+    out->l_exc = (int64_t)hc.l_exc;
+    out->raster_kept = (int64_t)hc.raster_total;
+    out->raster_dropped = (int64_t)hc.raster_dropped;
+    out->error = hc.error;
+    out->reserved = 0;
+    return SNN_OK;
+}
+
+int snn_net_info(const snn_net *net, uint32_t *n_neurons, int64_t *n_synapses, size_t *device_bytes)
+{
+    if (!net) { set_error("net is NULL"); return SNN_EINVAL; }
+    if (n_neurons) *n_neurons = net->N;
+    if (n_synapses) *n_synapses = net->S;
+    if (device_bytes) *device_bytes = net->bytes_held;
+    return SNN_OK;
+}
+
+int snn_set_profile(snn_net *net, int on)
+{
+    if (!net) { set_error("net is NULL"); return SNN_EINVAL; }
+    net->profile = on != 0;
+    for (int k = 0; k < kKinds; ++k) { net->prof_ms[k] = 0; net->prof_n[k] = 0; }
+    net->ev_used = 0;
+    return SNN_OK;
+}
+
+int snn_read_profile(snn_net *net, snn_profile *out)
+{
+    if (!net || !out) { set_error("NULL argument"); return SNN_EINVAL; }
+    for (int k = 0; k < kKinds; ++k) {
+        out->launches[k] = net->prof_n[k];
+        out->ms[k] = net->prof_ms[k];
+    }
+    return SNN_OK;
+}
+
+// checkpoint layout: header, then the arrays in the order listed below
+struct StateHeader {
+    uint32_t magic, version;
+    uint32_t N, D;
+    int64_t S;
+    int32_t t, raster_t0;
+    snn_config cfg;
+};
+
+int snn_save_state(snn_net *net, void *host_buf, size_t cap, size_t *n)
+{
+    if (!net || !n) { set_error("NULL argument"); return SNN_EINVAL; }
+    const size_t N = net->N, D = net->cfg.max_delay_ms, S = (size_t)net->S;
+    const size_t need = sizeof(StateHeader) + N * 24 + D * N * 4 + D * 8 + S * 8 + sizeof(DevCounters);
+    *n = need;
+    if (!host_buf) return SNN_OK;
+    if (cap < need) { set_error("checkpoint needs %zu bytes", need); return SNN_ETRUNC; }
+    char *p = (char *)host_buf;
+    StateHeader h{};
+    h.magic = kStateMagic;
+    h.version = 1;
+    h.N = net->N;
+    h.D = (uint32_t)D;
+    h.S = net->S;
+    h.t = net->t;
+    h.raster_t0 = net->t;
+    h.cfg = net->cfg;
+    std::memcpy(p, &h, sizeof h);
+    p += sizeof h;
+    cudaStream_t s = net->stream;
+    const DevNet &dn = net->dn;
+    const void *src[] = {dn.v, dn.u, dn.I, dn.hist, dn.last_old, dn.last_spike, dn.ring_ids, dn.ring_cnt, net->w, net->sd, net->ctr};
+    const size_t len[] = {N * 4, N * 4, N * 4, N * 4, N * 4, N * 4, D * N * 4, D * 8, S * 4, S * 4, sizeof(DevCounters)};
+    for (int k = 0; k < 11; ++k) {
+        if (len[k]) SNN_CUDA(cudaMemcpyAsync(p, src[k], len[k], cudaMemcpyDeviceToHost, s));
+        p += len[k];
+    }
+    SNN_CUDA(cudaStreamSynchronize(s));
+    return SNN_OK;
+}
+
+int snn_load_state(snn_net *net, const void *host_buf, size_t n)
+{
+    if (!net || !host_buf) { set_error("NULL argument"); return SNN_EINVAL; }
+    const size_t N = net->N, D = net->cfg.max_delay_ms, S = (size_t)net->S;
+    const size_t need = sizeof(StateHeader) + N * 24 + D * N * 4 + D * 8 + S * 8 + sizeof(DevCounters);
+    if (n < need) { set_error("checkpoint is %zu bytes, need %zu", n, need); return SNN_EINVAL; }
+    StateHeader h{};
+    std::memcpy(&h, host_buf, sizeof h);
+    if (h.magic != kStateMagic || h.version != 1 || h.N != net->N || h.D != D || h.S != net->S ||
+        std::memcmp(&h.cfg, &net->cfg, sizeof(snn_config)) != 0) {
+        set_error("checkpoint does not belong to a net of this configuration");
+        return SNN_EINVAL;
+    }
+    const char *p = (const char *)host_buf + sizeof h;
+    cudaStream_t s = net->stream;
+    DevNet &dn = net->dn;
+    void *dst[] = {dn.v, dn.u, dn.I, dn.hist, dn.last_old, dn.last_spike, dn.ring_ids, dn.ring_cnt, net->w, net->sd, net->ctr};
+    const size_t len[] = {N * 4, N * 4, N * 4, N * 4, N * 4, N * 4, D * N * 4, D * 8, S * 4, S * 4, sizeof(DevCounters)};
+    for (int k = 0; k < 11; ++k) {
+        if (len[k]) SNN_CUDA(cudaMemcpyAsync(dst[k], p, len[k], cudaMemcpyHostToDevice, s));
+        p += len[k];
+    }
+    SNN_CUDA(cudaStreamSynchronize(s));
+    net->t = h.t;
+    // the raster restarts at the checkpoint's step
+    DevCounters hc{};
+    std::memcpy(&hc, (const char *)host_buf + need - sizeof(DevCounters), sizeof hc);
+    hc.raster_total = 0;
+    hc.raster_dropped = 0;
+    hc.raster_first_drop_t = 0x7fffffff;
+    hc.t_slot[h.t & 1] = h.t;
+    SNN_CUDA(cudaMemcpyAsync(net->ctr, &hc, sizeof hc, cudaMemcpyHostToDevice, s));
+    if (dn.raster_step_off) SNN_CUDA(cudaMemsetAsync(dn.raster_step_off, 0, 8, s));
+    SNN_CUDA(cudaStreamSynchronize(s));
+    dn.raster_t0 = h.t;
+    drop_graphs(net);
+    return SNN_OK;
+}
+
+}  // extern "C"

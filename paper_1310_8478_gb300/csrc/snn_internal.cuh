@@ -1,0 +1,192 @@
+// snn_internal.cuh -- device-side data layout and helpers of the GB300 engine
+// for the DPSNN-STDP step (arXiv 1310.8478).  Private to csrc/.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "snn.h"
+
+namespace snn {
+
+constexpr int kLut = 256;            // STDP amounts for lags 0..255 (the rest are 0)
+constexpr int kDoffStride = 32;      // uint16 delay offsets per source row: [0..D], D <= 31
+constexpr int32_t kNever = -(1 << 30);  // "no spike yet" time stamp
+constexpr int kNeuronsPerThread = 8; // S2/S3: neurons handled by one thread
+constexpr int kKinds = 5;            // profiled kernel kinds: deliver, neuron, ltp, deriv, other
+
+// Device counters and per-step bookkeeping (one struct, device memory).
+struct DevCounters {
+    unsigned long long spikes, e_all, e_exc, l_exc;
+    unsigned long long raster_total, raster_dropped;
+    int error;
+    int raster_first_drop_t;
+    int step_cnt[2][4];              // [t & 1][exc, inh, all, -]: spikes of step t so far
+    int t_slot[2];                   // t_slot[t & 1] = t while step t runs
+    int pad[2];
+};
+
+// Everything a step kernel needs, passed by value.
+struct DevNet {
+    uint32_t N, npc, ne, C, D;       // neurons, per column, excitatory per column, columns, max delay
+    uint32_t uniform_m;              // > 0: row p starts at p * uniform_m (generated nets)
+    int64_t S;                       // synapses
+    const int64_t *row_off;          // [N + 1] first synapse of every source row
+    const uint16_t *doff;            // [N][kDoffStride]: synapses of delay <= d, d = 0..D
+    int32_t *tgt, *w, *sd;           // [S] forward synapses, rows sorted by delay
+    const int64_t *rin_off;          // [N + 1] reverse index (incoming excitatory synapses)
+    const uint64_t *rin;             // source | ordinal-in-row << 32 | delay << 48
+    float *v, *u;                    // [N] membrane potential, recovery variable
+    int32_t *I;                      // [N] Q16 input accumulated during S1/S2
+    uint32_t *hist;                  // [N] bit k: fired at step t - k
+    int32_t *last_old;               // [N] latest spike older than the 32-step window
+    int32_t *last_spike;             // [N] latest spike
+    int32_t *ring_ids;               // [D][N] spike ids of step s in slot s % D: exc from the
+                                     //         front, inh from the back
+    int32_t *ring_cnt;               // [D][2] exc / inh counts of every slot
+    int32_t *raster_gid;             // [raster_cap]
+    int64_t *raster_step_off;        // [steps + 1] raster index of the first spike of a step
+    uint64_t raster_cap;
+    int32_t raster_t0;               // step whose spikes sit at raster index 0
+    const int32_t *lut_p, *lut_m;    // [kLut] LTP / LTD amounts in Q16
+    const int32_t *stim_gid, *stim_q16;  // external events sorted by step
+    const int64_t *stim_off;         // [stim_t1 - stim_t0 + 1]
+    int32_t stim_t0, stim_t1;
+    DevCounters *ctr;
+    uint32_t thal_per_col;
+    int32_t thal_amp;
+    uint32_t seed_lo, seed_hi;
+    uint32_t flags;
+    int32_t deriv_bias, deriv_decay, wmax;
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 counter-based generator (Salmon et al., SC'11): ten rounds,
+// each a pair of 32x32->64 multiplies of words 0 and 2 by the Philox
+// multipliers, a word permutation, and xors with the round key; the key
+// advances by the golden-ratio and sqrt(3)-1 Weyl increments every round.
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+#ifdef __CUDA_ARCH__
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+#else
+        const uint32_t hi0 = (uint32_t)(((uint64_t)0xD2511F53u * c.x) >> 32);
+        const uint32_t hi1 = (uint32_t)(((uint64_t)0xCD9E8D57u * c.z) >> 32);
+#endif
+        const uint32_t lo0 = 0xD2511F53u * c.x;
+        const uint32_t lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// uniform integer in [0, n) from a 32-bit draw: high word of r * n
+__host__ __device__ __forceinline__ uint32_t draw_below(uint32_t r, uint32_t n)
+{
+#ifdef __CUDA_ARCH__
+    return __umulhi(r, n);
+#else
+    return (uint32_t)(((uint64_t)r * n) >> 32);
+#endif
+}
+
+// Network-generation parameters (Sec. 2, "Projection of synapses with
+// individual delay" and "Bidimensional arrays of neural columns").
+struct GenParams {
+    uint32_t npc, ne, m, D, gx, gy;
+    uint32_t ring_end[4];            // ordinals of ring k are [ring_end[k-1], ring_end[k])
+    uint32_t seed_lo, seed_hi;
+    int32_t w_exc0, w_inh0;
+};
+
+// Target and delay of ordinal j of source src.  Inhibitory sources: an
+// excitatory neuron of the own column, 1 ms.  Excitatory sources: delay
+// uniform in 1..D; ordinals are split into the own column and the three rings
+// of neighbours by the cumulative percentages; inside ring k the ordinal picks
+// one of the ring's four columns in turn (ring 1: +-x, +-y; ring 2: the
+// diagonals; ring 3: +-2x, +-2y, all modulo the torus); the target neuron is
+// uniform in the column, excluding the source itself.
+__host__ __device__ __forceinline__ void gen_synapse(const GenParams &g, uint32_t src, uint32_t j,
+                                                     uint32_t &target, uint32_t &delay)
+{
+    const uint4 r = philox10(make_uint4(src, j, 0u, 0u), g.seed_lo, g.seed_hi);
+    const uint32_t col = src / g.npc;
+    const uint32_t local = src - col * g.npc;
+    if (local >= g.ne) {
+        target = col * g.npc + draw_below(r.x, g.ne);
+        delay = 1;
+        return;
+    }
+    delay = 1 + draw_below(r.y, g.D);
+    uint32_t tcol = col;
+    if (j >= g.ring_end[0]) {
+        int ring = (j < g.ring_end[1]) ? 1 : (j < g.ring_end[2]) ? 2 : 3;
+        const uint32_t member = (j - g.ring_end[ring - 1]) & 3u;
+        // member 0..3 of the ring: (+s, 0), (-s, 0), (0, +s), (0, -s) for the
+        // axis rings (s = 1, 2); (+1, +1), (-1, +1), (+1, -1), (-1, -1) for ring 2
+        int dx, dy;
+        if (ring == 2) {
+            dx = (member & 1u) ? -1 : 1;
+            dy = (member & 2u) ? -1 : 1;
+        } else {
+            const int s = (ring == 1) ? 1 : 2;
+            const int sign = (member & 1u) ? -s : s;
+            dx = (member < 2u) ? sign : 0;
+            dy = (member < 2u) ? 0 : sign;
+        }
+        const int cx = (int)(col % g.gx), cy = (int)(col / g.gx);
+        int tx = (cx + dx) % (int)g.gx;
+        if (tx < 0) tx += (int)g.gx;
+        int ty = (cy + dy) % (int)g.gy;
+        if (ty < 0) ty += (int)g.gy;
+        tcol = (uint32_t)ty * g.gx + (uint32_t)tx;
+    }
+    uint32_t tl;
+    if (tcol == col) {
+        tl = draw_below(r.x, g.npc - 1);
+        tl += (tl >= local) ? 1u : 0u;
+    } else {
+        tl = draw_below(r.x, g.npc);
+    }
+    target = tcol * g.npc + tl;
+}
+
+__device__ __forceinline__ int64_t row_base(const DevNet &n, uint32_t p)
+{
+    return n.uniform_m ? (int64_t)p * n.uniform_m : n.row_off[p];
+}
+
+__device__ __forceinline__ unsigned lanemask_lt()
+{
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// ---- kernel entry points (defined in snn_build.cu / snn_step.cu) ----------
+__global__ void k_gen_rows(GenParams g, uint32_t n_rows, uint16_t *doff, int32_t *tgt, int32_t *w,
+                           int32_t *sd);
+__global__ void k_count_indeg(DevNet n, int32_t *indeg_exc, int32_t *indeg_inh);
+__global__ void k_scan_sums(const int32_t *in, uint32_t n, long long *block_sums);
+__global__ void k_scan_carry(long long *block_sums, uint32_t n_blocks);
+__global__ void k_scan_write(const int32_t *in, uint32_t n, const long long *block_sums, int64_t *out);
+__global__ void k_fill_reverse(DevNet n, int32_t *cursor, uint64_t *rin);
+__global__ void k_max2(const int32_t *a, const int32_t *b, uint32_t n, int32_t *out2);
+__global__ void k_init_state(DevNet n);
+__global__ void k_reset_weights(DevNet n, int32_t w_exc0, int32_t w_inh0);
+__global__ void k_read_rows(DevNet n, GenParams g, const uint8_t *canon_delay, uint32_t first,
+                            uint32_t count, int64_t out_base, int32_t *o_tgt, uint8_t *o_delay,
+                            int32_t *o_w, int32_t *o_sd);
+
+__global__ void k_deliver(DevNet n, const int *t_now);
+__global__ void k_neuron(DevNet n, const int *t_now);
+__global__ void k_ltp(DevNet n, const int *t_now, int *t_next);
+__global__ void k_deriv(DevNet n, uint32_t chunk);
+
+}  // namespace snn

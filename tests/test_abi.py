@@ -1,0 +1,79 @@
+"""The C-ABI library builds, loads and exports every symbol include/snn.h
+declares; host-side argument checks answer without a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import workloads
+from conftest import ROOT
+
+import paper_1310_8478_gb300 as eng
+from paper_1310_8478_gb300 import snn
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "snn.h")).read()
+    src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+    names = re.findall(r"\b(snn_[a-z0-9_]+)\s*\(", src)
+    return sorted(set(names))
+
+
+def test_library_builds_and_exports_every_declared_symbol():
+    path = eng.build()
+    assert os.path.exists(path)
+    lib = ctypes.CDLL(path)
+    names = declared_functions()
+    assert len(names) >= 20
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_binding_covers_the_header():
+    assert set(declared_functions()) == set(snn._SIGS)
+
+
+def test_config_struct_layout_matches_header():
+    # offsets the header fixes (all fields naturally aligned)
+    c = snn.SnnConfig
+    assert c.pct_ring.offset == 20 and c.max_delay_ms.offset == 36
+    assert c.a_plus_mv.offset == 56 and c.seed.offset == 112 and c.raster_capacity.offset == 128
+    assert ctypes.sizeof(c) == 136
+    assert ctypes.sizeof(snn.SnnCounters) == 64
+    assert ctypes.sizeof(snn.SnnLaunch) == 32
+
+
+def _rc_build(cfg, budget=0):
+    lib = snn.load()
+    h = ctypes.c_void_p()
+    c = snn.make_config(cfg)
+    return lib.snn_build_network(ctypes.byref(c), None, budget, ctypes.byref(h)), h
+
+
+@pytest.mark.parametrize("bad", [
+    dict(grid_x=0), dict(neurons_per_col=1), dict(exc_per_col=0), dict(fanout=0), dict(fanout=70000),
+    dict(pct_ring=(40, 30, 20, 11)), dict(max_delay_ms=0), dict(max_delay_ms=32), dict(wmax_q16=-1),
+    dict(tau_plus_ms=0.0), dict(a_minus_mv=-0.1), dict(flags=8),
+])
+def test_bad_config_is_rejected_before_any_device_work(bad):
+    rc, h = _rc_build(workloads.custom(**bad))
+    assert rc == snn.EINVAL and not h.value
+    assert snn.load().snn_last_error()
+
+
+def test_budget_is_checked_before_any_device_work():
+    rc, h = _rc_build(workloads.workload("grid64_m1125"), budget=1 << 30)
+    assert rc == snn.ENOMEM and not h.value
+    assert b"budget" in snn.load().snn_last_error()
+
+
+def test_strerror_covers_every_code():
+    lib = snn.load()
+    for code in (0, -1, -2, -3, -4, -5, -6, -7):
+        assert lib.snn_strerror(code) and lib.snn_strerror(code) != b"unknown error"
+    assert lib.snn_strerror(-99) == b"unknown error"
+
+
+def test_free_null_is_harmless():
+    snn.load().snn_free(None)

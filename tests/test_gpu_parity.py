@@ -1,0 +1,262 @@
+"""Parity of the CUDA path with the CPU oracle, through the C ABI.
+
+Bar: rasters, weights, derivatives, counters and the fp32 neuron state are
+bit-exact (integer Q16 synaptic arithmetic; fp32 neuron update with the same
+operation order and no contraction on either side).
+"""
+import numpy as np
+import pytest
+
+import workloads
+from conftest import stdp_tables
+
+pytestmark = pytest.mark.gpu
+
+FORCE_Q16 = 300 * 65536
+
+
+@pytest.fixture(scope="module")
+def eng():
+    import paper_1310_8478_gb300 as e
+    e.build()
+    return e
+
+
+def gpu_net(eng, cfg, **kw):
+    kw.setdefault("raster_capacity", 1 << 22)
+    return eng.Network(cfg, **kw)
+
+
+def assert_same_run(orc_sim, net, check_state=True):
+    ot, og = orc_sim.raster()
+    gt, gg = net.raster()
+    assert len(gt) == len(ot), (len(gt), len(ot))
+    assert np.array_equal(gt, ot) and np.array_equal(gg, og)
+    s = orc_sim.synapses()
+    w, sd = net.weights()
+    assert np.array_equal(w, s["w"])
+    assert np.array_equal(sd, s["sd"])
+    oc, gc = orc_sim.counters(), net.counters()
+    for k in ("spikes", "e_all", "e_exc", "l_exc"):
+        assert gc[k] == oc[k], (k, gc[k], oc[k])
+    assert gc["error"] == 0
+    if check_state:
+        on = orc_sim.neurons()
+        gn = net.neurons()
+        assert np.array_equal(gn["v"].view(np.int32), on["v"].view(np.int32))
+        assert np.array_equal(gn["u"].view(np.int32), on["u"].view(np.int32))
+
+
+# ---------------------------------------------------------------------------
+# construction
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("cfg", [
+    workloads.workload("col1_m100"),
+    workloads.custom(grid_x=3, grid_y=2, fanout=300, pct_ring=(40, 30, 20, 10), seed=12),
+    workloads.custom(grid_x=2, grid_y=2, fanout=1125, pct_ring=(40, 30, 20, 10), seed=4),
+    workloads.custom(grid_x=7, grid_y=6, neurons_per_col=50, exc_per_col=40, fanout=200,
+                     pct_ring=(76, 12, 8, 4), seed=11),
+], ids=["col1", "3x2", "2x2_m1125", "paper_mix"])
+def test_generated_network_equals_oracle(eng, orc, cfg):
+    o = orc.Oracle(cfg)
+    s = o.synapses()
+    with gpu_net(eng, cfg) as n:
+        g = n.synapses()
+        assert np.array_equal(g["tgt"], s["tgt"])
+        assert np.array_equal(g["delay"], s["delay"])
+        assert np.array_equal(g["w"], s["w"])
+        assert np.all(g["sd"] == 0)
+
+
+# ---------------------------------------------------------------------------
+# whole runs, bit-exact
+# ---------------------------------------------------------------------------
+def test_col1_m100_full_second_bitexact(eng, orc):
+    cfg = workloads.workload("col1_m100")
+    o = orc.Oracle(cfg)
+    o.run(1000)
+    with gpu_net(eng, cfg) as n:
+        n.run(1000)
+        assert_same_run(o, n)
+        assert n.counters()["spikes"] > 1000
+
+
+@pytest.mark.parametrize("gx,gy,m,T,seed", [
+    (2, 2, 60, 1100, 31),        # ring members coincide on a 2x2 torus; crosses a derivative update
+    (3, 3, 100, 1050, 32),
+    (1, 1, 100, 2100, 33),       # two derivative updates
+    (5, 3, 40, 1030, 34),        # ragged grid
+])
+def test_small_grids_bitexact_across_derivative_updates(eng, orc, gx, gy, m, T, seed):
+    cfg = workloads.custom(grid_x=gx, grid_y=gy, fanout=m,
+                           pct_ring=(40, 30, 20, 10) if gx * gy > 1 else (100, 0, 0, 0), seed=seed)
+    o = orc.Oracle(cfg)
+    o.run(T)
+    with gpu_net(eng, cfg) as n:
+        n.run(T)
+        assert_same_run(o, n)
+
+
+def test_grid8_m1125_onset_bitexact(eng, orc):
+    # the 8x8, M = 1125 workload over its first 32 ms: activity grows from the
+    # thalamic drive to ~70 % of the neurons firing every step
+    cfg = workloads.workload("grid8_m1125")
+    o = orc.Oracle(cfg)
+    o.run(32)
+    with gpu_net(eng, cfg) as n:
+        n.run(32)
+        assert_same_run(o, n)
+        assert n.counters()["spikes"] > 100000
+
+
+@pytest.mark.parametrize("flag_pair", [("STDP_OFF", 1, 1), ("DELIVERY_OFF", 2, 2)])
+def test_debug_flags_bitexact(eng, orc, flag_pair):
+    _, of, gf = flag_pair
+    cfg = workloads.custom(grid_x=2, grid_y=1, fanout=100, pct_ring=(40, 30, 20, 10), seed=41, flags=gf)
+    o = orc.Oracle(cfg, flags=of)
+    o.run(600)
+    with gpu_net(eng, cfg) as n:
+        n.run(600)
+        assert_same_run(o, n)
+
+
+# ---------------------------------------------------------------------------
+# STDP through the device path (explicit networks + forced spikes)
+# ---------------------------------------------------------------------------
+def _pair_cfg():
+    return workloads.custom(grid_x=1, grid_y=1, neurons_per_col=2, exc_per_col=2, fanout=1,
+                            pct_ring=(100, 0, 0, 0), thal_per_col_per_ms=0, deriv_period_ms=0)
+
+
+@pytest.mark.parametrize("d", [1, 7, 20])
+def test_stdp_pair_closed_form_on_gpu(eng, d):
+    ltp, ltd = stdp_tables()
+    net = dict(row_off=[0, 1, 1], tgt=[1], delay=[d], w=[0])
+    t_pre = 60
+    for lag in range(-40, 41):
+        t_post = t_pre + d + lag
+        with gpu_net(eng, _pair_cfg(), explicit=net) as n:
+            n.set_stimulus([t_pre, t_post], [0, 1], [FORCE_Q16] * 2)
+            n.run(max(t_pre + d, t_post) + 3)
+            t, g = n.raster()
+            assert sorted(zip(t.tolist(), g.tolist())) == sorted([(t_pre, 0), (t_post, 1)])
+            sd = int(n.weights()[1][0])
+            assert sd == (ltp[lag] if lag >= 0 else -ltd[-lag]), (d, lag)
+
+
+def test_explicit_trains_equal_oracle(eng, orc):
+    # random small explicit networks with forced spike trains and random rows
+    rng = np.random.default_rng(7)
+    for trial in range(6):
+        n_neu, ne = 12, 9
+        rows = [int(rng.integers(0, 6)) for _ in range(n_neu)]
+        row_off = np.concatenate([[0], np.cumsum(rows)]).astype(np.int64)
+        S = int(row_off[-1])
+        tgt = rng.integers(0, n_neu, S).astype(np.int32)
+        dl = rng.integers(1, 21, S).astype(np.uint8)
+        w = rng.integers(-3 * 65536, 3 * 65536, S).astype(np.int32)
+        cfg = workloads.custom(grid_x=1, grid_y=1, neurons_per_col=n_neu, exc_per_col=ne, fanout=1,
+                               pct_ring=(100, 0, 0, 0), thal_per_col_per_ms=0, deriv_period_ms=150,
+                               seed=100 + trial)
+        ex = dict(row_off=row_off, tgt=tgt, delay=dl, w=w)
+        st_t = rng.integers(0, 400, 60)
+        st_g = rng.integers(0, n_neu, 60)
+        st_q = rng.integers(0, 40 * 65536, 60)
+        o = orc.Oracle(cfg, explicit=ex)
+        o.set_stimulus(st_t, st_g, st_q)
+        o.run(420)
+        with gpu_net(eng, cfg, explicit=ex) as n:
+            n.set_stimulus(st_t, st_g, st_q)
+            n.run(420)
+            assert_same_run(o, n)
+
+
+# ---------------------------------------------------------------------------
+# layout invariance (Sec. 3: identical spikes for any distribution of the
+# network): any launch shape, with or without graphs, gives identical results
+# ---------------------------------------------------------------------------
+SHAPES = [
+    dict(deliver_block=256, deliver_blocks_per_sm=8, neuron_block=256, ltp_block=256, ltp_blocks_per_sm=8,
+         graph_steps=50),
+    dict(deliver_block=64, deliver_blocks_per_sm=1, neuron_block=32, ltp_block=32, ltp_blocks_per_sm=1,
+         graph_steps=1),
+    dict(deliver_block=1024, deliver_blocks_per_sm=3, neuron_block=1024, ltp_block=512, ltp_blocks_per_sm=5,
+         graph_steps=20, deriv_block=64),
+]
+
+
+def test_layout_invariance_under_launch_shapes(eng):
+    cfg = workloads.custom(grid_x=3, grid_y=2, fanout=200, pct_ring=(40, 30, 20, 10), seed=51)
+    ref = None
+    for shape in SHAPES:
+        with gpu_net(eng, cfg) as n:
+            n.set_launch(**shape)
+            n.run(1010)
+            r = (n.raster(), n.weights(), n.counters()["e_all"])
+        if ref is None:
+            ref = r
+        else:
+            assert np.array_equal(r[0][0], ref[0][0]) and np.array_equal(r[0][1], ref[0][1])
+            assert np.array_equal(r[1][0], ref[1][0]) and np.array_equal(r[1][1], ref[1][1])
+            assert r[2] == ref[2]
+
+
+def test_step_by_step_equals_run(eng):
+    cfg = workloads.workload("col1_m100")
+    with gpu_net(eng, cfg) as a, gpu_net(eng, cfg) as b:
+        a.run(230)
+        for _ in range(230):
+            b.step()
+        assert np.array_equal(a.raster()[1], b.raster()[1])
+        assert np.array_equal(a.weights()[1], b.weights()[1])
+
+
+# ---------------------------------------------------------------------------
+# checkpoint / resume, host end-to-end call
+# ---------------------------------------------------------------------------
+def test_checkpoint_resume_is_bitexact(eng):
+    cfg = workloads.custom(grid_x=2, grid_y=2, fanout=100, pct_ring=(40, 30, 20, 10), seed=61)
+    with gpu_net(eng, cfg) as a:
+        a.run(1200)
+        ref_r = a.raster(600, 1200)
+        ref_w = a.weights()
+    with gpu_net(eng, cfg) as b:
+        b.run(600)
+        blob = b.save_state()
+    with gpu_net(eng, cfg) as c:
+        c.load_state(blob)
+        assert c.counters()["t"] == 600
+        c.run(600)
+        r = c.raster(600, 1200)
+        assert np.array_equal(r[0], ref_r[0]) and np.array_equal(r[1], ref_r[1])
+        w = c.weights()
+        assert np.array_equal(w[0], ref_w[0]) and np.array_equal(w[1], ref_w[1])
+
+
+def test_run_host_equals_run_and_raster(eng):
+    cfg = workloads.custom(grid_x=2, grid_y=2, fanout=100, pct_ring=(40, 30, 20, 10), seed=62)
+    with gpu_net(eng, cfg) as a, gpu_net(eng, cfg) as b:
+        a.run(300)
+        ref = a.raster(0, 300)
+        t1, g1 = b.run_host(150)
+        t2, g2 = b.run_host(150)
+        assert np.array_equal(np.concatenate([t1, t2]), ref[0])
+        assert np.array_equal(np.concatenate([g1, g2]), ref[1])
+
+
+def test_overflow_bound_is_enforced(eng):
+    cfg = workloads.custom(grid_x=1, grid_y=1, fanout=2000, wmax_q16=2 ** 30)
+    with pytest.raises(eng.SnnError) as e:
+        eng.Network(cfg)
+    assert e.value.code == -4
+
+
+def test_raster_capacity_overflow_is_reported(eng):
+    cfg = workloads.workload("col1_m100")
+    with gpu_net(eng, cfg, raster_capacity=100) as n:
+        n.run(400)
+        c = n.counters()
+        assert c["raster_kept"] == 100 and c["raster_dropped"] == c["spikes"] - 100
+        with pytest.raises(eng.SnnError) as e:
+            n.raster(0, 400)
+        assert e.value.code == -6
