@@ -188,7 +188,7 @@ def main():
     if rank == 0 and not args.no_cpu_baseline:
         cpu = oracle_sample(args.cpu_seconds)      # before any GPU work; same process, no fork
 
-    eng.build()
+    eng.build_engine()
     cfg = workloads.workload(args.workload)
     K, W = args.steps, args.warmup
     n_neurons = workloads.n_neurons(cfg)
@@ -200,6 +200,7 @@ def main():
         t_build = time.perf_counter() - t_build
         net.run(W)
         net.set_profile(True)
+        prof0 = net.profile()
         c0 = net.counters()
         clocks = ClockSampler(local_rank)
         barrier()
@@ -215,6 +216,7 @@ def main():
         ms = e0.elapsed_time(e1)
         c1 = net.counters()
         prof = net.profile()
+        prof1 = prof
         net.set_profile(False)
 
         # end-to-end leg: the same workload restarted, driven from host memory
@@ -269,24 +271,32 @@ def main():
     value = total_events / secs
     rate_hz = d_spikes / n_neurons / (K / 1000.0)
     n_exc_syn = cfg["grid_x"] * cfg["grid_y"] * cfg["exc_per_col"] * cfg["fanout"]
-    # algorithmic bytes per launch of each kernel (measurement)
-    n_deriv = prof["deriv"][0]
+    # algorithmic bytes moved by each kernel over the timed region (the
+    # per-unit figures are in the design doc): 8 B per delivered event (target +
+    # weight), 8 B per event on a plastic synapse (sd read + write), 12 B per
+    # potentiation visit, 16 B per plastic synapse per long-term update,
+    # 32 B per neuron per step
+    dd = {k: prof1[k] - prof0[k] for k in ("dense_steps", "dense_deriv_steps", "dense_events",
+                                             "dense_exc_events", "dense_ltp_visits")}
+    deriv_runs = prof["deriv"][0]
     alg = {
-        "deliver": (8.0 * d_events + 8.0 * d_exc) / max(1, prof["deliver"][0]),
-        "ltp": 12.0 * d_ltp / max(1, prof["ltp"][0]),
-        "neuron": 32.0 * n_neurons,
-        "deriv": 16.0 * n_exc_syn,
+        "deliver": 8.0 * (d_events - dd["dense_events"]) + 8.0 * (d_exc - dd["dense_exc_events"]),
+        "ltp": 12.0 * max(0, d_ltp - dd["dense_ltp_visits"]),
+        "neuron": 32.0 * n_neurons * prof["neuron"][0],
+        "deriv": 16.0 * n_exc_syn * max(0, deriv_runs - dd["dense_deriv_steps"]),
+        "dense": (8.0 * dd["dense_events"] + 8.0 * dd["dense_exc_events"] + 12.0 * dd["dense_ltp_visits"]
+                  + 16.0 * n_exc_syn * dd["dense_deriv_steps"]),
     }
     peak, peak_kind = measured_peaks()
-    kernel_ms = {k: prof[k][1] for k in ("deliver", "neuron", "ltp", "deriv")}
+    names = ("deliver", "neuron", "ltp", "deriv", "dense")
+    kernel_ms = {k: prof[k][1] for k in names}
     dom = max(kernel_ms, key=kernel_ms.get)
-    avg_ms = prof[dom][1] / max(1, prof[dom][0])
-    achieved = alg[dom] / (avg_ms / 1000.0) / 1e9
+    achieved = alg[dom] / (kernel_ms[dom] / 1000.0) / 1e9
     per_kernel = {k: {"launches": prof[k][0], "ms": round(prof[k][1], 3),
                       "share": round(prof[k][1] / max(1e-9, sum(kernel_ms.values())), 4),
-                      "alg_gbs": round(alg[k] / (prof[k][1] / max(1, prof[k][0]) / 1000.0) / 1e9, 1)
-                      if prof[k][0] else None}
-                  for k in ("deliver", "neuron", "ltp", "deriv")}
+                      "alg_gbs": round(alg[k] / (prof[k][1] / 1000.0) / 1e9, 1) if prof[k][1] > 0 else None}
+                  for k in names}
+    per_kernel["dense"]["steps_taken"] = dd["dense_steps"]
     line = {
         "metric": "synaptic events/s", "value": value, "unit": "events/s", "n_gpus": world, "steps": K,
         "warmup": W, "ms_per_step": ms / K, "higher_is_better": True,
@@ -305,7 +315,7 @@ def main():
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
                      "traffic": None},
         "kernels": per_kernel,
-        "gpu_launches": int(sum(prof[k][0] for k in ("deliver", "neuron", "ltp", "deriv"))),
+        "gpu_launches": int(sum(prof[k][0] for k in names)),
         "build_s": round(t_build, 2),
         "e2e": e2e,
         "cpu_baseline": None if cpu is None else {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")},

@@ -110,20 +110,29 @@ typedef struct {
  * Zero fields keep the current value.
  */
 typedef struct {
-    uint32_t deliver_block;          /* threads per block of S1 (multiple of 32) */
+    uint32_t deliver_block;          /* threads per block of the event-driven delivery (multiple of 32) */
     uint32_t deliver_blocks_per_sm;
-    uint32_t neuron_block;           /* threads per block of S2/S3 */
-    uint32_t ltp_block;              /* threads per block of S4 */
+    uint32_t neuron_block;           /* threads per block of the neuron update */
+    uint32_t ltp_block;              /* threads per block of the event-driven potentiation */
     uint32_t ltp_blocks_per_sm;
     uint32_t deriv_block;
-    uint32_t graph_steps;            /* steps per captured CUDA graph; even; 0 = keep, 1 = no graphs */
-    uint32_t reserved;
+    uint32_t graph_steps;            /* steps per captured CUDA graph; even; 1 = no graphs */
+    uint32_t dense_block;            /* threads per block of the dense synapse pass (32..512) */
+    uint32_t dense_rows;             /* source rows per block of the dense pass */
+    uint32_t dense_permille;         /* a step takes the dense pass when at least this many
+                                        neurons per 1000 fired in the step before; 1001 = never */
 } snn_launch;
 
-/* Per-kernel device time collected while profiling is on (CUDA events). */
+/* Per-kernel device time collected while profiling is on (CUDA events), and
+   the work the dense synapse pass did (always counted). */
 typedef struct {
-    int64_t launches[5];             /* deliver, neuron, ltp, deriv, other */
+    int64_t launches[5];             /* deliver, neuron, ltp, deriv, dense */
     double ms[5];
+    int64_t dense_steps;             /* steps that took the dense pass */
+    int64_t dense_deriv_steps;       /* of which closed a plasticity period */
+    int64_t dense_events;            /* synaptic events delivered by the dense pass */
+    int64_t dense_exc_events;
+    int64_t dense_ltp_visits;        /* potentiation visits done by the dense pass */
 } snn_profile;
 
 typedef struct snn_net snn_net;

@@ -6,4 +6,4 @@ from .snn import (  # noqa: F401
     snn_build_network, snn_build_network_explicit, snn_step, snn_run, snn_free,
     snn_read_raster, snn_read_weights, STDP_OFF, DELIVERY_OFF,
 )
-from .build import build  # noqa: F401
+from .build import build as build_engine  # noqa: F401

@@ -93,6 +93,10 @@ struct snn_net {
     DevCounters *ctr = nullptr;
     int32_t *lut = nullptr;
     int64_t raster_steps_cap = 0;   // entries of dn.raster_step_off
+    uint16_t *tgt16 = nullptr;
+    int32_t *nbr = nullptr;
+    bool ltp_owed = false;          // the last step's LTP has not been applied yet
+    bool dense_ok = false;          // the dense pass can run on this net
     // stimulus
     size_t stim_cap = 0;
     int64_t stim_off_cap = 0;
@@ -210,12 +214,13 @@ int build_luts(const snn_config *c, std::vector<int32_t> &lut)
     const double amp[2] = {c->a_plus_mv, c->a_minus_mv};
     const double tau[2] = {c->tau_plus_ms, c->tau_minus_ms};
     for (int s = 0; s < 2; ++s) {
-        for (int k = 0; k <= kLut; ++k) {
+        for (int k = 0; k < kLut; ++k) {
             const double x = amp[s] * std::exp(-(double)k / tau[s]) * 65536.0;
             const long long q = std::llround(x);
-            if (k == kLut) {
+            if (k == kLut - 1) {
+                // lags of 255 and more all read the last entry: it must be 0
                 if (q != 0) {
-                    set_error("STDP window longer than %d ms (amount at lag %d is %lld)", kLut, kLut, q);
+                    set_error("STDP window longer than %d ms (amount at lag %d is %lld)", kLut - 1, k, q);
                     return SNN_EINVAL;
                 }
             } else {
@@ -237,7 +242,8 @@ size_t footprint(const snn_config *c, uint32_t N, int64_t S, int64_t n_rin, bool
 {
     const size_t D = c->max_delay_ms;
     size_t b = 0;
-    b += (size_t)S * 12;                          // tgt, w, sd
+    b += (size_t)S * ((!explicit_net && c->neurons_per_col <= kMaxCompactNpc) ? 10 : 12);  // tgt, w, sd
+    b += (size_t)c->grid_x * c->grid_y * kSlotStride * 4;                                  // neighbour table
     b += (size_t)N * kDoffStride * 2;             // delay offsets
     b += ((size_t)N + 1) * 8 * 2;                 // row_off, rin_off
     b += (size_t)n_rin * 8;                       // reverse index
@@ -249,12 +255,31 @@ size_t footprint(const snn_config *c, uint32_t N, int64_t S, int64_t n_rin, bool
     return b;
 }
 
+uint32_t dense_threshold(uint32_t n_neurons, uint32_t permille)
+{
+    if (permille > 1000) return 0xffffffffu;
+    const uint64_t v = ((uint64_t)n_neurons * permille + 999) / 1000;
+    return (uint32_t)std::max<uint64_t>(1, v);
+}
+
 int alloc_common(snn_net *net)
 {
     const uint32_t N = net->N;
     const uint32_t D = net->cfg.max_delay_ms;
     DevNet &dn = net->dn;
-    SNN_TRY(dalloc_t(net, (size_t)net->S, &net->tgt));
+    const bool compact = !net->explicit_net && net->cfg.neurons_per_col <= kMaxCompactNpc;
+    if (compact) SNN_TRY(dalloc_t(net, (size_t)net->S, &net->tgt16));
+    else SNN_TRY(dalloc_t(net, (size_t)net->S, &net->tgt));
+    const uint32_t C = net->cfg.grid_x * net->cfg.grid_y;
+    SNN_TRY(dalloc_t(net, (size_t)C * kSlotStride, &net->nbr));
+    {
+        std::vector<int32_t> nb((size_t)C * kSlotStride);
+        for (uint32_t c = 0; c < C; ++c)
+            for (uint32_t sl = 0; sl < (uint32_t)kSlotStride; ++sl)
+                nb[(size_t)c * kSlotStride + sl] =
+                    (int32_t)(sl < (uint32_t)kSlots ? slot_column(c, sl, net->cfg.grid_x, net->cfg.grid_y) : c);
+        SNN_CUDA(cudaMemcpy(net->nbr, nb.data(), nb.size() * 4, cudaMemcpyHostToDevice));
+    }
     SNN_TRY(dalloc_t(net, (size_t)net->S, &net->w));
     SNN_TRY(dalloc_t(net, (size_t)net->S, &net->sd));
     SNN_TRY(dalloc_t(net, (size_t)N * kDoffStride, &net->doff));
@@ -280,10 +305,13 @@ int alloc_common(snn_net *net)
     dn.ne = net->cfg.exc_per_col;
     dn.C = net->cfg.grid_x * net->cfg.grid_y;
     dn.D = D;
+    dn.D_inh = 1;
     dn.S = net->S;
     dn.row_off = net->row_off;
     dn.doff = net->doff;
     dn.tgt = net->tgt;
+    dn.tgt16 = net->tgt16;
+    dn.nbr = net->nbr;
     dn.w = net->w;
     dn.sd = net->sd;
     dn.rin_off = net->rin_off;
@@ -298,9 +326,26 @@ int alloc_common(snn_net *net)
     dn.seed_lo = (uint32_t)(net->cfg.seed & 0xffffffffu);
     dn.seed_hi = (uint32_t)(net->cfg.seed >> 32);
     dn.flags = net->cfg.flags;
+    dn.deriv_period = net->cfg.deriv_period_ms;
+    dn.dense_rows = net->launch.dense_rows;
+    dn.dense_min_spikes = dense_threshold(net->N, net->launch.dense_permille);
     dn.deriv_bias = net->cfg.deriv_bias_q16;
     dn.deriv_decay = net->cfg.deriv_decay_q16;
     dn.wmax = net->cfg.wmax_q16;
+    return SNN_OK;
+}
+
+// whether the dense pass can run with the current launch shape (shared memory)
+int setup_dense(snn_net *net)
+{
+    net->dense_ok = false;
+    if (!net->tgt16 || net->cfg.neurons_per_col > kDenseMaxNpc) return SNN_OK;
+    const size_t bytes = dense_smem_bytes(net->cfg.neurons_per_col, net->launch.dense_block);
+    int optin = 0;
+    SNN_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, net->device));
+    if (bytes + 1024 > (size_t)optin) return SNN_OK;
+    SNN_CUDA(cudaFuncSetAttribute(k_dense, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    net->dense_ok = true;
     return SNN_OK;
 }
 
@@ -370,6 +415,7 @@ int finish_build(snn_net *net)
     k_init_state<<<g, 256, 0, s>>>(dn);
     DevCounters hc{};
     hc.raster_first_drop_t = 0x7fffffff;
+    hc.ltp_pending = kNoPending;
     hc.t_slot[0] = 0;
     hc.t_slot[1] = 0;
     SNN_CUDA(cudaMemcpyAsync(net->ctr, &hc, sizeof hc, cudaMemcpyHostToDevice, s));
@@ -377,6 +423,8 @@ int finish_build(snn_net *net)
     if (dn.raster_step_off) SNN_CUDA(cudaMemsetAsync(dn.raster_step_off, 0, 8, s));
     SNN_CUDA(cudaGetLastError());
     SNN_CUDA(cudaStreamSynchronize(s));
+    SNN_TRY(setup_dense(net));
+    if (!net->dense_ok) net->dn.dense_min_spikes = 0xffffffffu;
     return SNN_OK;
 }
 
@@ -399,6 +447,9 @@ int start_net(const snn_config *cfg, void *cuda_stream, size_t budget, snn_net *
     net->launch.ltp_blocks_per_sm = 8;
     net->launch.deriv_block = 256;
     net->launch.graph_steps = 50;
+    net->launch.dense_block = 512;
+    net->launch.dense_rows = 250;
+    net->launch.dense_permille = 50;
     (void)cuda_stream;
     return SNN_OK;
 }
@@ -446,7 +497,30 @@ cudaEvent_t next_event(snn_net *net, int kind)
     return net->ev_pool[net->ev_used++];
 }
 
-void launch_step(snn_net *net, int32_t t, bool deriv)
+int deriv_grid_x(const snn_net *net)
+{
+    const DevNet &dn = net->dn;
+    const int64_t per_col = dn.uniform_m ? (int64_t)dn.ne * dn.uniform_m
+                                         : net->S / std::max<uint32_t>(1u, dn.C) + 1;
+    return (int)std::min<int64_t>(1024, std::max<int64_t>(1, per_col / ((int64_t)net->launch.deriv_block * 4)));
+}
+
+// the LTP (and long-term update) owed by step t - 1, applied before any read
+void launch_flush(snn_net *net)
+{
+    const DevNet &dn = net->dn;
+    cudaStream_t s = net->stream;
+    const int32_t t = net->t;
+    const int *t_now = &net->ctr->t_slot[t & 1];
+    k_ltp<<<grid_for(net, net->launch.ltp_blocks_per_sm), net->launch.ltp_block, 0, s>>>(dn, t_now, 1);
+    const uint32_t P = net->cfg.deriv_period_ms;
+    if (P && t > 0 && (uint32_t)t % P == 0)
+        k_deriv<<<dim3(deriv_grid_x(net), dn.C), net->launch.deriv_block, 0, s>>>(dn, t_now, 1);
+    const int32_t none = kNoPending;
+    cudaMemcpyAsync(&net->ctr->ltp_pending, &none, sizeof none, cudaMemcpyHostToDevice, s);
+}
+
+void launch_step(snn_net *net, int32_t t)
 {
     const DevNet &dn = net->dn;
     cudaStream_t s = net->stream;
@@ -454,31 +528,35 @@ void launch_step(snn_net *net, int32_t t, bool deriv)
     int *t_next = &net->ctr->t_slot[(t & 1) ^ 1];
     const snn_launch &L = net->launch;
     const bool prof = net->profile;
-    cudaEvent_t e0, e1;
+    const uint32_t P = net->cfg.deriv_period_ms;
+    auto mark = [&](int kind) {
+        if (prof) cudaEventRecord(next_event(net, kind), s);
+    };
+    // [S4(t-1) S5(t-1) S1(t)]: event-driven kernels and the dense pass; the
+    // device picks one of the two (the other returns at once)
+    mark(2);
+    k_ltp<<<grid_for(net, L.ltp_blocks_per_sm), L.ltp_block, 0, s>>>(dn, t_now, 0);
+    mark(2);
+    if (P && t > 0 && (uint32_t)t % P == 0) {
+        mark(3);
+        k_deriv<<<dim3(deriv_grid_x(net), dn.C), L.deriv_block, 0, s>>>(dn, t_now, 0);
+        mark(3);
+    }
+    mark(0);
+    k_deliver<<<grid_for(net, L.deliver_blocks_per_sm), L.deliver_block, 0, s>>>(dn, t_now);
+    mark(0);
+    if (net->dense_ok) {
+        const uint32_t chunks = (dn.npc + L.dense_rows - 1) / L.dense_rows;
+        mark(4);
+        k_dense<<<dn.C * chunks, L.dense_block, dense_smem_bytes(dn.npc, L.dense_block), s>>>(dn, t_now);
+        mark(4);
+    }
+    // [S2(t) S3(t)]
     const int nb_neuron = (int)((net->N + L.neuron_block * kNeuronsPerThread - 1) /
                                 (L.neuron_block * kNeuronsPerThread));
-    // S1
-    if (prof) { e0 = next_event(net, 0); cudaEventRecord(e0, s); }
-    k_deliver<<<grid_for(net, L.deliver_blocks_per_sm), L.deliver_block, 0, s>>>(dn, t_now);
-    if (prof) { e1 = next_event(net, 0); cudaEventRecord(e1, s); }
-    // S2 + S3
-    if (prof) { e0 = next_event(net, 1); cudaEventRecord(e0, s); }
-    k_neuron<<<nb_neuron, L.neuron_block, 0, s>>>(dn, t_now);
-    if (prof) { e1 = next_event(net, 1); cudaEventRecord(e1, s); }
-    // S4
-    if (prof) { e0 = next_event(net, 2); cudaEventRecord(e0, s); }
-    k_ltp<<<grid_for(net, L.ltp_blocks_per_sm), L.ltp_block, 0, s>>>(dn, t_now, t_next);
-    if (prof) { e1 = next_event(net, 2); cudaEventRecord(e1, s); }
-    // S5
-    if (deriv) {
-        const uint32_t C = dn.C;
-        const int64_t per_col = (int64_t)dn.ne * (dn.uniform_m ? dn.uniform_m : 1);
-        uint32_t gx = (uint32_t)std::min<int64_t>(1024, std::max<int64_t>(1, per_col / ((int64_t)L.deriv_block * 4)));
-        if (!dn.uniform_m) gx = (uint32_t)std::min<int64_t>(1024, std::max<int64_t>(1, (net->S / std::max(1u, C)) / L.deriv_block + 1));
-        if (prof) { e0 = next_event(net, 3); cudaEventRecord(e0, s); }
-        k_deriv<<<dim3(gx, C), L.deriv_block, 0, s>>>(dn, 0);
-        if (prof) { e1 = next_event(net, 3); cudaEventRecord(e1, s); }
-    }
+    mark(1);
+    k_neuron<<<nb_neuron, L.neuron_block, 0, s>>>(dn, t_now, t_next);
+    mark(1);
 }
 
 uint32_t effective_graph_len(const snn_net *net)
@@ -492,11 +570,16 @@ uint32_t effective_graph_len(const snn_net *net)
     return 0;
 }
 
+// variant 1: the chunk's first step closes a plasticity period (its k_deriv
+// launch is part of the graph)
 int build_graph(snn_net *net, int variant, uint32_t L)
 {
+    // steps t0 .. t0+L-1 with t0 = P (variant 1) or 0 (no positive multiple of
+    // P inside, as L divides P); only the parity of t and t mod P matter
+    const int32_t base_t = variant ? (int32_t)net->cfg.deriv_period_ms : 0;
     cudaGraph_t g = nullptr;
     SNN_CUDA(cudaStreamBeginCapture(net->stream, cudaStreamCaptureModeThreadLocal));
-    for (uint32_t k = 0; k < L; ++k) launch_step(net, (int32_t)k, variant && k + 1 == L);
+    for (uint32_t k = 0; k < L; ++k) launch_step(net, base_t + (int32_t)k);
     cudaError_t e = cudaStreamEndCapture(net->stream, &g);
     if (e != cudaSuccess) {
         set_error("graph capture failed: %s", cudaGetErrorString(e));
@@ -555,7 +638,7 @@ int run_steps(snn_net *net, uint32_t n_ms)
     while (left > 0) {
         const int32_t t = net->t;
         if (L >= 2 && (uint32_t)t % L == 0 && left >= L) {
-            const int variant = (P && ((uint32_t)t + L) % P == 0) ? 1 : 0;
+            const int variant = (P && t > 0 && (uint32_t)t % P == 0) ? 1 : 0;
             if (net->graphs_dirty) {
                 for (int i = 0; i < 2; ++i)
                     if (net->graph[i]) { cudaGraphExecDestroy(net->graph[i]); net->graph[i] = nullptr; }
@@ -565,14 +648,27 @@ int run_steps(snn_net *net, uint32_t n_ms)
             SNN_CUDA(cudaGraphLaunch(net->graph[variant], net->stream));
             net->t += (int32_t)L;
             left -= L;
+            net->ltp_owed = true;
         } else {
-            launch_step(net, t, P && ((uint32_t)t + 1) % P == 0);
+            launch_step(net, t);
             SNN_CUDA(cudaGetLastError());
             net->t += 1;
             left -= 1;
+            net->ltp_owed = true;
         }
     }
     return finish_run(net);
+}
+
+// apply the LTP / long-term update owed by the last step (before reads)
+int flush_owed(snn_net *net)
+{
+    if (!net->ltp_owed) return SNN_OK;
+    launch_flush(net);
+    SNN_CUDA(cudaGetLastError());
+    SNN_CUDA(cudaStreamSynchronize(net->stream));
+    net->ltp_owed = false;
+    return SNN_OK;
 }
 
 int set_stimulus_impl(snn_net *net, const snn_stimulus *ev, size_t n)
@@ -764,7 +860,7 @@ int snn_build_network(const snn_config *cfg, void *cuda_stream, size_t hbm_budge
     g.w_inh0 = c.w_inh0_q16;
     const int gr = grid_for(net, 16);
     k_fill_row_off<<<gr, 256, 0, net->stream>>>(net->row_off, net->N, c.fanout);
-    k_gen_rows<<<gr, 256, 0, net->stream>>>(g, net->N, net->doff, net->tgt, net->w, net->sd);
+    k_gen_rows<<<gr, 256, 0, net->stream>>>(g, net->N, net->doff, net->tgt, net->tgt16, net->w, net->sd);
     if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(net->stream) != cudaSuccess) {
         set_error("network generation failed: %s", cudaGetErrorString(cudaGetLastError()));
         return fail(SNN_ECUDA);
@@ -820,6 +916,11 @@ int snn_build_network_explicit(const snn_config *cfg, const int64_t *host_row_of
     if ((r = alloc_common(net)) != SNN_OK) return fail(r);
     if ((r = dalloc_t(net, (size_t)std::max<int64_t>(S, 1), &net->canon_delay)) != SNN_OK) return fail(r);
     net->dn.uniform_m = 0;
+    net->dn.D_inh = 1;
+    for (uint32_t p = 0; p < N; ++p)
+        if ((p % net->cfg.neurons_per_col) >= net->cfg.exc_per_col)
+            for (int64_t k = host_row_off[p]; k < host_row_off[p + 1]; ++k)
+                net->dn.D_inh = std::max<uint32_t>(net->dn.D_inh, host_delay[k]);
     // stable counting sort of every row by delay
     std::vector<int32_t> tg((size_t)S), ww((size_t)S);
     std::vector<uint16_t> doff((size_t)N * kDoffStride, 0);
@@ -883,11 +984,22 @@ int snn_set_launch(snn_net *net, const snn_launch *launch)
     L.ltp_blocks_per_sm = pick(launch->ltp_blocks_per_sm, L.ltp_blocks_per_sm);
     L.deriv_block = pick(launch->deriv_block, L.deriv_block);
     L.graph_steps = pick(launch->graph_steps, L.graph_steps);
+    L.dense_block = pick(launch->dense_block, L.dense_block);
+    L.dense_rows = pick(launch->dense_rows, L.dense_rows);
+    L.dense_permille = pick(launch->dense_permille, L.dense_permille);
     for (uint32_t b : {L.deliver_block, L.neuron_block, L.ltp_block, L.deriv_block}) {
         if (b < 32 || b > 1024 || b % 32) { set_error("block sizes must be multiples of 32 in 32..1024"); return SNN_EINVAL; }
     }
+    if (L.dense_block < 32 || L.dense_block > 512 || L.dense_block % 32) {
+        set_error("dense_block must be a multiple of 32 in 32..512");
+        return SNN_EINVAL;
+    }
     if (L.deliver_blocks_per_sm > 64 || L.ltp_blocks_per_sm > 64) { set_error("blocks per SM must be <= 64"); return SNN_EINVAL; }
     net->launch = L;
+    net->dn.dense_rows = L.dense_rows;
+    net->dn.dense_min_spikes = dense_threshold(net->N, L.dense_permille);
+    SNN_TRY(setup_dense(net));
+    if (!net->dense_ok) net->dn.dense_min_spikes = 0xffffffffu;
     drop_graphs(net);
     return SNN_OK;
 }
@@ -950,12 +1062,14 @@ int snn_reset(snn_net *net)
     k_init_state<<<g, 256, 0, s>>>(net->dn);
     DevCounters hc{};
     hc.raster_first_drop_t = 0x7fffffff;
+    hc.ltp_pending = kNoPending;
     SNN_CUDA(cudaMemcpyAsync(net->ctr, &hc, sizeof hc, cudaMemcpyHostToDevice, s));
     SNN_CUDA(cudaMemsetAsync(net->dn.ring_cnt, 0, (size_t)2 * net->cfg.max_delay_ms * 4, s));
     if (net->dn.raster_step_off) SNN_CUDA(cudaMemsetAsync(net->dn.raster_step_off, 0, 8, s));
     SNN_CUDA(cudaGetLastError());
     SNN_CUDA(cudaStreamSynchronize(s));
     net->t = 0;
+    net->ltp_owed = false;
     net->dn.raster_t0 = 0;
     net->dn.stim_t0 = net->dn.stim_t1 = 0;
     drop_graphs(net);
@@ -1009,6 +1123,7 @@ int snn_read_synapses(snn_net *net, uint32_t first, uint32_t count, int32_t *hos
 {
     if (!net) { set_error("net is NULL"); return SNN_EINVAL; }
     if ((uint64_t)first + count > net->N) { set_error("row range out of bounds"); return SNN_EINVAL; }
+    SNN_TRY(flush_owed(net));
     std::vector<int64_t> ro(2);
     SNN_CUDA(cudaMemcpyAsync(&ro[0], net->row_off + first, 8, cudaMemcpyDeviceToHost, net->stream));
     SNN_CUDA(cudaMemcpyAsync(&ro[1], net->row_off + first + count, 8, cudaMemcpyDeviceToHost, net->stream));
@@ -1113,6 +1228,13 @@ int snn_read_profile(snn_net *net, snn_profile *out)
         out->launches[k] = net->prof_n[k];
         out->ms[k] = net->prof_ms[k];
     }
+    DevCounters hc{};
+    SNN_TRY(read_counters_raw(net, &hc));
+    out->dense_steps = (int64_t)hc.dense_steps;
+    out->dense_deriv_steps = (int64_t)hc.dense_deriv_steps;
+    out->dense_events = (int64_t)hc.dense_e_all;
+    out->dense_exc_events = (int64_t)hc.dense_e_exc;
+    out->dense_ltp_visits = (int64_t)hc.dense_l_exc;
     return SNN_OK;
 }
 
@@ -1132,6 +1254,7 @@ int snn_save_state(snn_net *net, void *host_buf, size_t cap, size_t *n)
     const size_t need = sizeof(StateHeader) + N * 24 + D * N * 4 + D * 8 + S * 8 + sizeof(DevCounters);
     *n = need;
     if (!host_buf) return SNN_OK;
+    SNN_TRY(flush_owed(net));
     if (cap < need) { set_error("checkpoint needs %zu bytes", need); return SNN_ETRUNC; }
     char *p = (char *)host_buf;
     StateHeader h{};
@@ -1181,6 +1304,7 @@ int snn_load_state(snn_net *net, const void *host_buf, size_t n)
     }
     SNN_CUDA(cudaStreamSynchronize(s));
     net->t = h.t;
+    net->ltp_owed = false;
     // the raster restarts at the checkpoint's step
     DevCounters hc{};
     std::memcpy(&hc, (const char *)host_buf + need - sizeof(DevCounters), sizeof hc);
@@ -1188,6 +1312,8 @@ int snn_load_state(snn_net *net, const void *host_buf, size_t n)
     hc.raster_dropped = 0;
     hc.raster_first_drop_t = 0x7fffffff;
     hc.t_slot[h.t & 1] = h.t;
+    hc.ltp_pending = kNoPending;
+    hc.done_blocks = 0;
     SNN_CUDA(cudaMemcpyAsync(net->ctr, &hc, sizeof hc, cudaMemcpyHostToDevice, s));
     if (dn.raster_step_off) SNN_CUDA(cudaMemsetAsync(dn.raster_step_off, 0, 8, s));
     SNN_CUDA(cudaStreamSynchronize(s));

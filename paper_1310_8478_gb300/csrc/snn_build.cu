@@ -16,8 +16,8 @@ namespace snn {
 // per delay, write the delay offsets, then place every synapse at
 // row_base + offset(delay) + rank, stable in the ordinal j.
 // ---------------------------------------------------------------------------
-__global__ void k_gen_rows(GenParams g, uint32_t n_rows, uint16_t *doff, int32_t *tgt, int32_t *w,
-                           int32_t *sd)
+__global__ void k_gen_rows(GenParams g, uint32_t n_rows, uint16_t *doff, int32_t *tgt, uint16_t *tgt16,
+                           int32_t *w, int32_t *sd)
 {
     constexpr int kWarps = 8;        // launched with 256 threads
     __shared__ int s_cnt[kWarps][32];
@@ -30,8 +30,8 @@ __global__ void k_gen_rows(GenParams g, uint32_t n_rows, uint16_t *doff, int32_t
         s_cnt[warp][lane] = 0;
         __syncwarp();
         for (uint32_t j = lane; j < g.m; j += 32) {
-            uint32_t t, d;
-            gen_synapse(g, p, j, t, d);
+            uint32_t t, d, sl;
+            gen_synapse(g, p, j, t, d, sl);
             atomicAdd(&s_cnt[warp][d], 1);
         }
         __syncwarp();
@@ -49,8 +49,8 @@ __global__ void k_gen_rows(GenParams g, uint32_t n_rows, uint16_t *doff, int32_t
         for (uint32_t j0 = 0; j0 < g.m; j0 += 32) {
             const uint32_t j = j0 + lane;
             const bool active = j < g.m;
-            uint32_t t = 0, d = 0;
-            if (active) gen_synapse(g, p, j, t, d);
+            uint32_t t = 0, d = 0, sl = 0;
+            if (active) gen_synapse(g, p, j, t, d, sl);
             const unsigned peers = __match_any_sync(0xffffffffu, d);   // d = 0: inactive lanes
             const int rank = __popc(peers & lt);
             const int start = s_cur[warp][d];
@@ -58,7 +58,8 @@ __global__ void k_gen_rows(GenParams g, uint32_t n_rows, uint16_t *doff, int32_t
             if (active && rank == __popc(peers) - 1) s_cur[warp][d] = start + __popc(peers);
             if (active) {
                 const int64_t pos = base + start + rank;
-                tgt[pos] = (int32_t)t;
+                if (tgt16) tgt16[pos] = (uint16_t)((sl << 12) | (t % g.npc));
+                else tgt[pos] = (int32_t)t;
                 w[pos] = exc ? g.w_exc0 : g.w_inh0;
                 sd[pos] = 0;
             }
@@ -76,8 +77,9 @@ __global__ void k_count_indeg(DevNet n, int32_t *indeg_exc, int32_t *indeg_inh)
     for (uint32_t p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < n.N; p += warps) {
         const bool exc = (p % n.npc) < n.ne;
         int32_t *deg = exc ? indeg_exc : indeg_inh;
+        const uint32_t col = p / n.npc;
         const int64_t lo = n.row_off[p], hi = n.row_off[p + 1];
-        for (int64_t k = lo + lane; k < hi; k += 32) atomicAdd(&deg[n.tgt[k]], 1);
+        for (int64_t k = lo + lane; k < hi; k += 32) atomicAdd(&deg[target_gid(n, col, k)], 1);
     }
 }
 
@@ -174,11 +176,12 @@ __global__ void k_fill_reverse(DevNet n, int32_t *cursor, uint64_t *rin)
     for (uint32_t p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < n.N; p += warps) {
         if ((p % n.npc) >= n.ne) continue;
         const int64_t base = n.row_off[p];
+        const uint32_t col = p / n.npc;
         const uint16_t *off = n.doff + (size_t)p * kDoffStride;
         for (uint32_t d = 1; d <= n.D; ++d) {
             const uint32_t lo = off[d - 1], hi = off[d];
             for (uint32_t k = lo + lane; k < hi; k += 32) {
-                const int32_t t = n.tgt[base + k];
+                const uint32_t t = target_gid(n, col, base + k);
                 const int slot = atomicAdd(&cursor[t], 1);
                 rin[n.rin_off[t] + slot] = (uint64_t)p | ((uint64_t)k << 32) | ((uint64_t)d << 48);
             }
@@ -247,13 +250,13 @@ __global__ void k_read_rows(DevNet n, GenParams g, const uint8_t *canon_delay, u
             if (canon_delay) {
                 d = canon_delay[lo + j];
             } else {
-                uint32_t t;
-                gen_synapse(g, p, (uint32_t)j, t, d);
+                uint32_t t, sl;
+                gen_synapse(g, p, (uint32_t)j, t, d, sl);
             }
             const int64_t pos = lo + off[d - 1] + used[d];
             used[d]++;
             const int64_t o = lo - out_base + j;
-            if (o_tgt) o_tgt[o] = n.tgt[pos];
+            if (o_tgt) o_tgt[o] = (int32_t)target_gid(n, p / n.npc, pos);
             if (o_delay) o_delay[o] = (uint8_t)d;
             if (o_w) o_w[o] = n.w[pos];
             if (o_sd) o_sd[o] = n.sd[pos];

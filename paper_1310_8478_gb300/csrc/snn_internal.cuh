@@ -13,7 +13,12 @@ constexpr int kLut = 256;            // STDP amounts for lags 0..255 (the rest a
 constexpr int kDoffStride = 32;      // uint16 delay offsets per source row: [0..D], D <= 31
 constexpr int32_t kNever = -(1 << 30);  // "no spike yet" time stamp
 constexpr int kNeuronsPerThread = 8; // S2/S3: neurons handled by one thread
-constexpr int kKinds = 5;            // profiled kernel kinds: deliver, neuron, ltp, deriv, other
+constexpr int kKinds = 5;            // profiled kernel kinds: deliver, neuron, ltp, deriv, dense
+constexpr int kSlots = 13;           // own column + 3 rings of 4 neighbour columns
+constexpr int kSlotStride = 16;      // entries per column in the neighbour table
+constexpr int32_t kNoPending = -(1 << 30);  // ltp_pending value when no LTP is owed
+constexpr uint32_t kMaxCompactNpc = 4096;    // 12-bit local ids in the compact target format
+constexpr uint32_t kDenseMaxNpc = 3200;      // staged columns must fit in shared memory
 
 // Device counters and per-step bookkeeping (one struct, device memory).
 struct DevCounters {
@@ -23,17 +28,24 @@ struct DevCounters {
     int raster_first_drop_t;
     int step_cnt[2][4];              // [t & 1][exc, inh, all, -]: spikes of step t so far
     int t_slot[2];                   // t_slot[t & 1] = t while step t runs
-    int pad[2];
+    int ltp_pending;                 // step whose LTP (and long-term update) is still owed
+    unsigned done_blocks;            // blocks of k_neuron finished (last block closes the step)
+    unsigned long long dense_e_all, dense_e_exc, dense_l_exc;  // work done by the dense pass
+    unsigned long long dense_steps, dense_deriv_steps;
 };
 
 // Everything a step kernel needs, passed by value.
 struct DevNet {
     uint32_t N, npc, ne, C, D;       // neurons, per column, excitatory per column, columns, max delay
+    uint32_t D_inh;                  // largest delay of an inhibitory synapse (1 for generated nets)
     uint32_t uniform_m;              // > 0: row p starts at p * uniform_m (generated nets)
     int64_t S;                       // synapses
     const int64_t *row_off;          // [N + 1] first synapse of every source row
     const uint16_t *doff;            // [N][kDoffStride]: synapses of delay <= d, d = 0..D
-    int32_t *tgt, *w, *sd;           // [S] forward synapses, rows sorted by delay
+    int32_t *tgt;                    // [S] target gid (explicit nets / big columns), or NULL
+    uint16_t *tgt16;                 // [S] compact target: slot << 12 | local id, or NULL
+    const int32_t *nbr;              // [C][kSlotStride] global column of every slot
+    int32_t *w, *sd;                 // [S] weight, STDP derivative; rows sorted by delay
     const int64_t *rin_off;          // [N + 1] reverse index (incoming excitatory synapses)
     const uint64_t *rin;             // source | ordinal-in-row << 32 | delay << 48
     float *v, *u;                    // [N] membrane potential, recovery variable
@@ -58,6 +70,9 @@ struct DevNet {
     uint32_t seed_lo, seed_hi;
     uint32_t flags;
     int32_t deriv_bias, deriv_decay, wmax;
+    uint32_t deriv_period;
+    uint32_t dense_min_spikes;       // spikes of step t-1 from which step t takes the dense pass
+    uint32_t dense_rows;             // source rows per block of the dense pass
 };
 
 // ---------------------------------------------------------------------------
@@ -105,19 +120,48 @@ struct GenParams {
     int32_t w_exc0, w_inh0;
 };
 
-// Target and delay of ordinal j of source src.  Inhibitory sources: an
+// slot (0: own column, 1 + 4 (ring - 1) + member) -> column offset on the torus:
+// ring 1 members (+1,0) (-1,0) (0,+1) (0,-1); ring 2 (+1,+1) (-1,+1) (+1,-1)
+// (-1,-1); ring 3 (+2,0) (-2,0) (0,+2) (0,-2)
+__host__ __device__ __forceinline__ void slot_offset(uint32_t slot, int &dx, int &dy)
+{
+    if (slot == 0) { dx = dy = 0; return; }
+    const uint32_t ring = 1 + (slot - 1) / 4, member = (slot - 1) & 3u;
+    if (ring == 2) {
+        dx = (member & 1u) ? -1 : 1;
+        dy = (member & 2u) ? -1 : 1;
+    } else {
+        const int s = (ring == 1) ? 1 : 2;
+        const int sign = (member & 1u) ? -s : s;
+        dx = (member < 2u) ? sign : 0;
+        dy = (member < 2u) ? 0 : sign;
+    }
+}
+
+__host__ __device__ __forceinline__ uint32_t slot_column(uint32_t col, uint32_t slot, uint32_t gx, uint32_t gy)
+{
+    int dx, dy;
+    slot_offset(slot, dx, dy);
+    int tx = ((int)(col % gx) + dx) % (int)gx;
+    if (tx < 0) tx += (int)gx;
+    int ty = ((int)(col / gx) + dy) % (int)gy;
+    if (ty < 0) ty += (int)gy;
+    return (uint32_t)ty * gx + (uint32_t)tx;
+}
+
+// Target, delay and slot of ordinal j of source src.  Inhibitory sources: an
 // excitatory neuron of the own column, 1 ms.  Excitatory sources: delay
 // uniform in 1..D; ordinals are split into the own column and the three rings
-// of neighbours by the cumulative percentages; inside ring k the ordinal picks
-// one of the ring's four columns in turn (ring 1: +-x, +-y; ring 2: the
-// diagonals; ring 3: +-2x, +-2y, all modulo the torus); the target neuron is
-// uniform in the column, excluding the source itself.
+// of neighbours by the cumulative percentages; inside a ring the ordinal picks
+// the ring's four columns in turn; the target neuron is uniform in the
+// column, excluding the source itself.
 __host__ __device__ __forceinline__ void gen_synapse(const GenParams &g, uint32_t src, uint32_t j,
-                                                     uint32_t &target, uint32_t &delay)
+                                                     uint32_t &target, uint32_t &delay, uint32_t &slot)
 {
     const uint4 r = philox10(make_uint4(src, j, 0u, 0u), g.seed_lo, g.seed_hi);
     const uint32_t col = src / g.npc;
     const uint32_t local = src - col * g.npc;
+    slot = 0;
     if (local >= g.ne) {
         target = col * g.npc + draw_below(r.x, g.ne);
         delay = 1;
@@ -126,26 +170,9 @@ __host__ __device__ __forceinline__ void gen_synapse(const GenParams &g, uint32_
     delay = 1 + draw_below(r.y, g.D);
     uint32_t tcol = col;
     if (j >= g.ring_end[0]) {
-        int ring = (j < g.ring_end[1]) ? 1 : (j < g.ring_end[2]) ? 2 : 3;
-        const uint32_t member = (j - g.ring_end[ring - 1]) & 3u;
-        // member 0..3 of the ring: (+s, 0), (-s, 0), (0, +s), (0, -s) for the
-        // axis rings (s = 1, 2); (+1, +1), (-1, +1), (+1, -1), (-1, -1) for ring 2
-        int dx, dy;
-        if (ring == 2) {
-            dx = (member & 1u) ? -1 : 1;
-            dy = (member & 2u) ? -1 : 1;
-        } else {
-            const int s = (ring == 1) ? 1 : 2;
-            const int sign = (member & 1u) ? -s : s;
-            dx = (member < 2u) ? sign : 0;
-            dy = (member < 2u) ? 0 : sign;
-        }
-        const int cx = (int)(col % g.gx), cy = (int)(col / g.gx);
-        int tx = (cx + dx) % (int)g.gx;
-        if (tx < 0) tx += (int)g.gx;
-        int ty = (cy + dy) % (int)g.gy;
-        if (ty < 0) ty += (int)g.gy;
-        tcol = (uint32_t)ty * g.gx + (uint32_t)tx;
+        const uint32_t ring = (j < g.ring_end[1]) ? 1u : (j < g.ring_end[2]) ? 2u : 3u;
+        slot = 1u + 4u * (ring - 1u) + ((j - g.ring_end[ring - 1]) & 3u);
+        tcol = slot_column(col, slot, g.gx, g.gy);
     }
     uint32_t tl;
     if (tcol == col) {
@@ -155,6 +182,24 @@ __host__ __device__ __forceinline__ void gen_synapse(const GenParams &g, uint32_
         tl = draw_below(r.x, g.npc);
     }
     target = tcol * g.npc + tl;
+}
+
+// target gid of synapse k whose source lives in column src_col
+__device__ __forceinline__ uint32_t target_gid(const DevNet &n, uint32_t src_col, int64_t k)
+{
+    if (n.tgt16) {
+        const uint32_t v = n.tgt16[k];
+        return (uint32_t)n.nbr[src_col * kSlotStride + (v >> 12)] * n.npc + (v & 0xfffu);
+    }
+    return (uint32_t)n.tgt[k];
+}
+
+// the step takes the dense pass when enough neurons fired in the previous step
+__device__ __forceinline__ bool dense_selected(const DevNet &n, int t)
+{
+    if (!n.tgt16 || n.npc > kDenseMaxNpc || t < 1) return false;
+    const int slot = (t - 1) % (int)n.D;
+    return (uint32_t)(n.ring_cnt[2 * slot] + n.ring_cnt[2 * slot + 1]) >= n.dense_min_spikes;
 }
 
 __device__ __forceinline__ int64_t row_base(const DevNet &n, uint32_t p)
@@ -170,8 +215,8 @@ __device__ __forceinline__ unsigned lanemask_lt()
 }
 
 // ---- kernel entry points (defined in snn_build.cu / snn_step.cu) ----------
-__global__ void k_gen_rows(GenParams g, uint32_t n_rows, uint16_t *doff, int32_t *tgt, int32_t *w,
-                           int32_t *sd);
+__global__ void k_gen_rows(GenParams g, uint32_t n_rows, uint16_t *doff, int32_t *tgt, uint16_t *tgt16,
+                           int32_t *w, int32_t *sd);
 __global__ void k_count_indeg(DevNet n, int32_t *indeg_exc, int32_t *indeg_inh);
 __global__ void k_scan_sums(const int32_t *in, uint32_t n, long long *block_sums);
 __global__ void k_scan_carry(long long *block_sums, uint32_t n_blocks);
@@ -185,8 +230,11 @@ __global__ void k_read_rows(DevNet n, GenParams g, const uint8_t *canon_delay, u
                             int32_t *o_w, int32_t *o_sd);
 
 __global__ void k_deliver(DevNet n, const int *t_now);
-__global__ void k_neuron(DevNet n, const int *t_now);
-__global__ void k_ltp(DevNet n, const int *t_now, int *t_next);
-__global__ void k_deriv(DevNet n, uint32_t chunk);
+__global__ void k_dense(DevNet n, const int *t_now);
+__global__ void k_neuron(DevNet n, const int *t_now, int *t_next);
+__global__ void k_ltp(DevNet n, const int *t_now, int force);
+__global__ void k_deriv(DevNet n, const int *t_now, int force);
+
+size_t dense_smem_bytes(uint32_t npc, uint32_t block);
 
 }  // namespace snn

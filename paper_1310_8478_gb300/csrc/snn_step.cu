@@ -1,19 +1,27 @@
 // snn_step.cu -- the per-millisecond step of the DPSNN-STDP engine on GB300.
 //
 // Paper, Sec. 2 "Mixed time-driven and event driven simulation": synapses are
-// event driven (only synapses of neurons that fired are touched), neurons are
-// time driven (every neuron is updated every step).  One step t runs
-//   k_deliver  S1: spikes emitted at t - d reach their delay-d synapses
-//              (steps 2.3-2.5), depression of excitatory synapses against the
-//              target's latest spike (2.6); thalamic and external drive.
-//   k_neuron   S2: Izhikevich update of every neuron (2.7); S3: the neurons
-//              that fired are compacted into the delay ring and the raster.
-//   k_ltp      S4: potentiation of the incoming excitatory synapses of every
-//              neuron that fired at t (2.1), through the reverse index.
-//   k_deriv    S5: every deriv_period steps, w += bias + sd, sd *= decay.
-// All synaptic arithmetic is int32 Q16, so the order of the atomic additions
-// does not change any result; the neuron update is IEEE fp32 with one
-// rounding per operation (explicit _rn intrinsics, no contraction).
+// event driven, neurons time driven.  The cycle 2.1-2.7 is taken as
+//   S1 delivery of the spikes due at t + LTD       (2.3-2.6)
+//   S2 thalamic drive + Izhikevich update          (2.7)
+//   S3 spike compaction into the ring and raster   (2.2)
+//   S4 LTP of the incoming synapses of the spikers (2.1)
+//   S5 long-term update at the end of each period
+// The device runs step t as
+//   [S4(t-1) S5(t-1) S1(t)] then [S2(t) S3(t)]
+// i.e. the potentiation owed by the previous step travels with this step's
+// delivery, so that one pass over the synapses can do both.  Two
+// interchangeable implementations of the first bracket exist:
+//   sparse (event driven): k_ltp (reverse index of the spikers of t-1),
+//       k_deriv, k_deliver ((spike, delay) items over the delay buckets);
+//   dense: k_dense streams every source row once, in per-synapse order
+//       LTP(t-1) -> long-term update -> delivery + LTD(t), with the target
+//       columns' input and post-spike lags staged in shared memory.
+// The choice is taken on the device from the number of spikes of step t-1
+// (every kernel of the step reads the same count); both give bit-identical
+// results because all synaptic arithmetic is int32 and the per-synapse order
+// of the updates is the same.  An LTP still owed when a run ends is applied
+// by the host-side flush (k_ltp + k_deriv with force = 1) before any read.
 #include "snn_internal.cuh"
 
 namespace snn {
@@ -39,49 +47,22 @@ __device__ __forceinline__ T block_sum(T x)
     return r;   // valid in thread 0
 }
 
-// ---------------------------------------------------------------------------
-// S1: delivery + LTD.  Work items are (spike, delay) pairs: every excitatory
-// spike of step t - d for d = 1..D and every inhibitory spike of step t - 1
-// (inhibitory synapses all have delay 1).  One warp walks an item's
-// delay-bucketed segment with coalesced loads; lanes add the weight into the
-// target's Q16 input with a fire-and-forget L2 reduction and, for plastic
-// synapses, subtract the LTD amount at lag t - last_spike[target].
-// ---------------------------------------------------------------------------
-__global__ void k_deliver(DevNet n, const int *t_now)
+__device__ __forceinline__ int32_t deriv_w(const DevNet &n, int32_t w, int32_t s)
 {
-    __shared__ int32_t s_lut[kLut];
-    __shared__ int s_start[34];       // item prefix over the lists: 0..D-1 exc(d = 1..D), D inh(d = 1)
-    __shared__ const int32_t *s_list[33];
-    __shared__ int s_inh[33];
-    const int t = *t_now;
-    const bool stdp = !(n.flags & SNN_STDP_OFF);
-    for (int i = threadIdx.x; i < kLut; i += blockDim.x) s_lut[i] = n.lut_m[i];
-    if (threadIdx.x == 0) {
-        int acc = 0;
-        const int nl = (int)n.D + 1;
-        for (int l = 0; l < nl; ++l) {
-            const int d = (l < (int)n.D) ? l + 1 : 1;
-            const bool inh = (l == (int)n.D);
-            int cnt = 0;
-            const int32_t *list = nullptr;
-            if (!(n.flags & SNN_DELIVERY_OFF) && t - d >= 0) {
-                const int slot = (t - d) % (int)n.D;
-                cnt = n.ring_cnt[2 * slot + (inh ? 1 : 0)];
-                list = n.ring_ids + (size_t)slot * n.N;
-            }
-            s_start[l] = acc;
-            s_list[l] = list;
-            s_inh[l] = inh;
-            acc += cnt;
-        }
-        s_start[nl] = acc;
-    }
-    __syncthreads();
+    long long nw = (long long)w + n.deriv_bias + s;
+    nw = nw < 0 ? 0 : (nw > n.wmax ? n.wmax : nw);
+    return (int32_t)nw;
+}
 
-    // thalamic drive: thal_per_col events per column (Philox keyed by (t, col))
-    // and the external events of step t
-    const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x;
-    const uint32_t gthreads = gridDim.x * blockDim.x;
+__device__ __forceinline__ int32_t deriv_sd(const DevNet &n, int32_t s)
+{
+    return (int32_t)(((long long)s * n.deriv_decay + 32768) >> 16);
+}
+
+// thalamic drive (thal_per_col events per column, Philox keyed by (t, col))
+// and the external events of step t, by the threads of a whole grid
+__device__ __forceinline__ void drive(const DevNet &n, int t, uint32_t gtid, uint32_t gthreads)
+{
     const uint32_t n_thal = n.C * n.thal_per_col;
     for (uint32_t e = gtid; e < n_thal; e += gthreads) {
         const uint32_t col = e / n.thal_per_col, k = e - col * n.thal_per_col;
@@ -92,8 +73,49 @@ __global__ void k_deliver(DevNet n, const int *t_now)
         const int64_t lo = n.stim_off[t - n.stim_t0], hi = n.stim_off[t - n.stim_t0 + 1];
         for (int64_t e = lo + gtid; e < hi; e += gthreads) red_add(&n.I[n.stim_gid[e]], n.stim_q16[e]);
     }
+}
 
-    const int nl = (int)n.D + 1;
+// ---------------------------------------------------------------------------
+// sparse S1: work items are (spike, delay) pairs -- every excitatory spike of
+// step t - d for d = 1..D and every inhibitory spike of step t - d for
+// d = 1..D_inh (generated nets: inhibitory synapses all have delay 1).  One
+// warp walks an item's delay bucket with coalesced loads; lanes add the
+// weight into the target's Q16 input with a fire-and-forget L2 reduction and,
+// on plastic synapses, subtract the LTD amount at lag t - last_spike[target].
+// ---------------------------------------------------------------------------
+__global__ void k_deliver(DevNet n, const int *t_now)
+{
+    __shared__ int32_t s_lut[kLut];
+    __shared__ int s_start[2 * 32 + 1];
+    __shared__ const int32_t *s_list[2 * 32];
+    const int t = *t_now;
+    if (dense_selected(n, t)) return;
+    const bool stdp = !(n.flags & SNN_STDP_OFF);
+    const int nl = (int)(n.D + n.D_inh);
+    for (int i = threadIdx.x; i < kLut; i += blockDim.x) s_lut[i] = n.lut_m[i];
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int l = 0; l < nl; ++l) {
+            const bool inh = l >= (int)n.D;
+            const int d = inh ? l - (int)n.D + 1 : l + 1;
+            int cnt = 0;
+            const int32_t *list = nullptr;
+            if (!(n.flags & SNN_DELIVERY_OFF) && t - d >= 0) {
+                const int slot = (t - d) % (int)n.D;
+                cnt = n.ring_cnt[2 * slot + (inh ? 1 : 0)];
+                list = n.ring_ids + (size_t)slot * n.N;
+            }
+            s_start[l] = acc;
+            s_list[l] = list;
+            acc += cnt;
+        }
+        s_start[nl] = acc;
+    }
+    __syncthreads();
+    const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t gthreads = gridDim.x * blockDim.x;
+    drive(n, t, gtid, gthreads);
+
     const int total = s_start[nl];
     const int lane = threadIdx.x & 31;
     const uint32_t warps = gthreads >> 5;
@@ -102,9 +124,10 @@ __global__ void k_deliver(DevNet n, const int *t_now)
         int l = 0;
         while (s_start[l + 1] <= (int)item) ++l;
         const int idx = (int)item - s_start[l];
-        const bool inh = s_inh[l];
-        const int d = inh ? 1 : l + 1;
+        const bool inh = l >= (int)n.D;
+        const int d = inh ? l - (int)n.D + 1 : l + 1;
         const uint32_t p = (uint32_t)(inh ? s_list[l][n.N - 1 - idx] : s_list[l][idx]);
+        const uint32_t col = p / n.npc;
         const uint16_t *off = n.doff + (size_t)p * kDoffStride;
         const int64_t base = row_base(n, p);
         const int64_t lo = base + off[d - 1], hi = base + off[d];
@@ -112,7 +135,7 @@ __global__ void k_deliver(DevNet n, const int *t_now)
         if (!inh) ev_exc += (unsigned long long)(hi - lo);
         if (!inh && stdp) {
             for (int64_t k = lo + lane; k < hi; k += 32) {
-                const int32_t tg = n.tgt[k];
+                const uint32_t tg = target_gid(n, col, k);
                 red_add(&n.I[tg], n.w[k]);
                 const int lag = t - n.last_spike[tg];          // >= 1
                 if (lag < kLut) {
@@ -121,10 +144,9 @@ __global__ void k_deliver(DevNet n, const int *t_now)
                 }
             }
         } else {
-            for (int64_t k = lo + lane; k < hi; k += 32) red_add(&n.I[n.tgt[k]], n.w[k]);
+            for (int64_t k = lo + lane; k < hi; k += 32) red_add(&n.I[target_gid(n, col, k)], n.w[k]);
         }
     }
-    // lane 0 of each warp counted the items; sum over the block
     if (lane != 0) ev_all = ev_exc = 0;
     const unsigned long long ba = block_sum(ev_all);
     const unsigned long long be = block_sum(ev_exc);
@@ -135,11 +157,242 @@ __global__ void k_deliver(DevNet n, const int *t_now)
 }
 
 // ---------------------------------------------------------------------------
+// sparse S4 for step t - 1: warp per neuron that fired at t - 1; lanes walk
+// its incoming excitatory synapses.  The nearest arrival with t_pre + d <=
+// t - 1 is the lowest set bit k >= d of the source's 32-step history (lag
+// k - d), else its latest older spike last_old (lag t - 1 - last_old - d).
+// ---------------------------------------------------------------------------
+__global__ void k_ltp(DevNet n, const int *t_now, int force)
+{
+    __shared__ int32_t s_lut[kLut];
+    const int t = *t_now;
+    const int tp = t - 1;
+    if (n.ctr->ltp_pending != tp || (n.flags & SNN_STDP_OFF)) return;
+    if (!force && dense_selected(n, t)) return;
+    for (int i = threadIdx.x; i < kLut; i += blockDim.x) s_lut[i] = n.lut_p[i];
+    __syncthreads();
+    const int slot = tp % (int)n.D;
+    const int ce = n.ring_cnt[2 * slot], ci = n.ring_cnt[2 * slot + 1];
+    const int total = ce + ci;
+    const int32_t *ring = n.ring_ids + (size_t)slot * n.N;
+    const int lane = threadIdx.x & 31;
+    const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t item = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; item < (uint32_t)total;
+         item += warps) {
+        const int32_t post = (int)item < ce ? ring[item] : ring[n.N - 1 - ((int)item - ce)];
+        const int64_t lo = n.rin_off[post], hi = n.rin_off[post + 1];
+        for (int64_t e = lo + lane; e < hi; e += 32) {
+            const uint64_t r = n.rin[e];
+            const uint32_t pre = (uint32_t)r;
+            const uint32_t ord = (uint32_t)(r >> 32) & 0xffffu;
+            const uint32_t d = (uint32_t)(r >> 48);
+            const uint32_t recent = n.hist[pre] & (0xffffffffu << d);
+            const int lag = recent ? (__ffs(recent) - 1 - (int)d) : (tp - n.last_old[pre] - (int)d);
+            if (lag < kLut) {
+                const int32_t a = s_lut[lag];
+                if (a) n.sd[row_base(n, pre) + ord] += a;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// sparse S5 closing step t - 1 (when t is a multiple of the period): over the
+// excitatory rows of column blockIdx.y (rows c*npc .. c*npc+ne-1 are
+// contiguous): w = clamp(w + bias + sd, 0, wmax), sd = (sd*decay + 2^15) >> 16.
+// ---------------------------------------------------------------------------
+__global__ void k_deriv(DevNet n, const int *t_now, int force)
+{
+    const int t = *t_now;
+    if (n.ctr->ltp_pending != t - 1) return;
+    if (!force && dense_selected(n, t)) return;
+    const uint32_t col = blockIdx.y;
+    const int64_t lo = row_base(n, col * n.npc);
+    const int64_t hi = n.uniform_m ? (int64_t)(col * n.npc + n.ne) * n.uniform_m
+                                   : n.row_off[col * n.npc + n.ne];
+    for (int64_t k = lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < hi;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t s = n.sd[k];
+        n.w[k] = deriv_w(n, n.w[k], s);
+        n.sd[k] = deriv_sd(n, s);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// dense [S4(t-1) S5(t-1) S1(t)] for compact nets.  Block = (column c, chunk of
+// dense_rows source rows of c).  Shared memory holds, for the 13 columns the
+// rows can reach (slots), the Q16 input accumulated by this block and the lag
+// t - last_spike of every neuron (saturated at 255; lag 1 <=> fired at t-1).
+// Warp per row; lanes walk the row's positions in order; every position's
+// delay bucket gives its per-bucket flags (deliver: the source fired at t - d;
+// LTP amount: from the source's history at t - 1).  Per synapse, in order:
+// sd += LTP amount if the target fired at t - 1; the long-term update if the
+// period ended at t - 1; delivery into the staged input and LTD.  The staged
+// input is flushed with one reduction per neuron touched.
+// ---------------------------------------------------------------------------
+size_t dense_smem_bytes(uint32_t npc, uint32_t block)
+{
+    const size_t warps = block / 32;
+    return 2 * kLut * 4                       // LTP / LTD tables
+           + (size_t)kSlots * npc * 4         // staged input
+           + warps * 32 * 4 * 3               // per-warp bucket offsets, flags, LTP amounts
+           + (((size_t)kSlots * npc + 15) & ~size_t(15));  // lags (bytes)
+}
+
+__global__ void __launch_bounds__(512) k_dense(DevNet n, const int *t_now)
+{
+    extern __shared__ int4 smem_i4[];
+    const int t = *t_now;
+    if (!dense_selected(n, t)) return;
+    const uint32_t npc = n.npc;
+    const uint32_t nwarps = blockDim.x >> 5;
+    int32_t *s_lutp = reinterpret_cast<int32_t *>(smem_i4);
+    int32_t *s_lutm = s_lutp + kLut;
+    int32_t *s_in = s_lutm + kLut;                              // [kSlots * npc]
+    int32_t *s_off = s_in + kSlots * npc;                       // [nwarps][32] bucket end offsets
+    uint32_t *s_flag = reinterpret_cast<uint32_t *>(s_off + nwarps * 32);  // [nwarps][32] 1: deliver
+    int32_t *s_amt = reinterpret_cast<int32_t *>(s_flag + nwarps * 32);    // [nwarps][32] LTP amount
+    uint8_t *s_lag = reinterpret_cast<uint8_t *>(s_amt + nwarps * 32);     // [kSlots * npc]
+    __shared__ uint32_t s_col[kSlots];
+
+    const bool stdp = !(n.flags & SNN_STDP_OFF);
+    const bool deliver_on = !(n.flags & SNN_DELIVERY_OFF);
+    const bool owed = n.ctr->ltp_pending == t - 1;
+    const bool ltp_on = owed && stdp;
+    const bool deriv_on = owed && n.deriv_period && (t % (int)n.deriv_period) == 0;
+    const uint32_t chunks = (npc + n.dense_rows - 1) / n.dense_rows;
+    const uint32_t col = blockIdx.x / chunks;
+    const uint32_t r0 = (blockIdx.x - col * chunks) * n.dense_rows;
+    const uint32_t r1 = min(npc, r0 + n.dense_rows);
+
+    if (threadIdx.x < kSlots) s_col[threadIdx.x] = (uint32_t)n.nbr[col * kSlotStride + threadIdx.x];
+    for (int i = threadIdx.x; i < kLut; i += blockDim.x) {
+        s_lutp[i] = n.lut_p[i];
+        s_lutm[i] = n.lut_m[i];
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < kSlots * npc; i += blockDim.x) {
+        const uint32_t sl = i / npc, loc = i - sl * npc;
+        const int lag = t - n.last_spike[s_col[sl] * npc + loc];
+        s_lag[i] = (uint8_t)min(lag, 255);
+        s_in[i] = 0;
+    }
+    __syncthreads();
+    drive(n, t, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int32_t *w_off = s_off + warp * 32;
+    uint32_t *w_flag = s_flag + warp * 32;
+    int32_t *w_amt = s_amt + warp * 32;
+    const int D = (int)n.D;
+    unsigned long long ev_all = 0, ev_exc = 0, visits = 0;
+    for (uint32_t r = r0 + warp; r < r1; r += nwarps) {
+        const uint32_t p = col * npc + r;
+        const bool exc = r < n.ne;
+        const uint32_t h = n.hist[p];                 // bit k: fired at t - 1 - k
+        const uint16_t *off = n.doff + (size_t)p * kDoffStride;
+        // lane d (1..D) prepares bucket d
+        int len = 0;
+        uint32_t fl = 0;
+        int32_t amt = 0;
+        if (lane >= 1 && lane <= D) {
+            const int lo = off[lane - 1], hi = off[lane];
+            len = hi - lo;
+            w_off[lane] = hi;
+            fl = (deliver_on && ((h >> (lane - 1)) & 1u)) ? 1u : 0u;
+            if (exc && ltp_on && len) {
+                const uint32_t recent = h & (0xffffffffu << lane);
+                const int lag = recent ? (__ffs(recent) - 1 - lane) : (t - 1 - n.last_old[p] - lane);
+                amt = lag < kLut ? s_lutp[lag] : 0;
+            }
+            w_flag[lane] = fl;
+            w_amt[lane] = amt;
+        }
+        const int delivered = fl ? len : 0;
+        const bool busy = __any_sync(0xffffffffu, fl != 0 || amt != 0) || (exc && deriv_on);
+        int dl = delivered;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) dl += __shfl_xor_sync(0xffffffffu, dl, o);
+        if (lane == 0) {
+            ev_all += (unsigned long long)dl;
+            if (exc) ev_exc += (unsigned long long)dl;
+        }
+        __syncwarp();
+        if (busy) {
+            const int m = off[D];
+            const int64_t base = row_base(n, p);
+            int d = 1;
+            for (int k = lane; k < m; k += 32) {
+                while (k >= w_off[d]) ++d;
+                const uint32_t f = w_flag[d];
+                const int32_t a = w_amt[d];
+                if (!exc) {
+                    if (f) {
+                        const uint32_t v = n.tgt16[base + k];
+                        atomicAdd(&s_in[(v >> 12) * npc + (v & 0xfffu)], n.w[base + k]);
+                    }
+                    continue;
+                }
+                if (!f && !a && !deriv_on) continue;
+                const int64_t pos = base + k;
+                const uint32_t v = n.tgt16[pos];
+                const uint32_t idx = (v >> 12) * npc + (v & 0xfffu);
+                const int lag = s_lag[idx];
+                const bool pot = a && lag == 1;
+                const int32_t dep = (f && stdp) ? s_lutm[lag] : 0;
+                if (!pot && !deriv_on && !f) continue;
+                if (ltp_on && lag == 1) visits++;
+                int32_t s = (pot || deriv_on || dep) ? n.sd[pos] : 0;
+                if (pot) s += a;
+                int32_t wv = 0;
+                if (deriv_on) {
+                    wv = deriv_w(n, n.w[pos], s);
+                    s = deriv_sd(n, s);
+                    n.w[pos] = wv;
+                } else if (f) {
+                    wv = n.w[pos];
+                }
+                if (f) atomicAdd(&s_in[idx], wv);
+                s -= dep;
+                if (pot || deriv_on || dep) n.sd[pos] = s;
+            }
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < kSlots * npc; i += blockDim.x) {
+        const int32_t v = s_in[i];
+        if (v) {
+            const uint32_t sl = i / npc;
+            red_add(&n.I[s_col[sl] * npc + (i - sl * npc)], v);
+        }
+    }
+    if (lane != 0) ev_all = ev_exc = 0;
+    const unsigned long long ba = block_sum(ev_all);
+    const unsigned long long be = block_sum(ev_exc);
+    const unsigned long long bv = block_sum(visits);
+    if (threadIdx.x == 0) {
+        if (ba) {
+            atomicAdd(&n.ctr->e_all, ba);
+            atomicAdd(&n.ctr->e_exc, be);
+            atomicAdd(&n.ctr->dense_e_all, ba);
+            atomicAdd(&n.ctr->dense_e_exc, be);
+        }
+        if (bv) atomicAdd(&n.ctr->dense_l_exc, bv);
+        if (blockIdx.x == 0) {
+            n.ctr->dense_steps += 1;
+            if (deriv_on) n.ctr->dense_deriv_steps += 1;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // S2 + S3: Izhikevich update (paper Sec. 2 "Spiking neuron model"; v in two
 // 0.5 ms Euler substeps, u in one 1 ms step, Sec. 3) of kNeuronsPerThread
-// neurons per thread, then one block-wide compaction of the neurons that
-// fired into ring slot t % D (exc ids from the front, inh ids from the back)
-// and into the raster.
+// neurons per thread, one block-wide compaction of the neurons that fired
+// into ring slot t % D (exc ids from the front, inh ids from the back) and
+// into the raster.  The last block to finish closes the step: ring counts,
+// counters, raster step offset, LTP owed for step t, next time stamp.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ bool izhikevich_step(float &v, float &u, int32_t iq, bool exc)
 {
@@ -171,13 +424,14 @@ __device__ __forceinline__ bool izhikevich_step(float &v, float &u, int32_t iq, 
     return false;
 }
 
-__global__ void k_neuron(DevNet n, const int *t_now)
+__global__ void k_neuron(DevNet n, const int *t_now, int *t_next)
 {
     const int t = *t_now;
     const int par = t & 1;
     const uint32_t tile = blockDim.x * kNeuronsPerThread;
     const uint32_t first = blockIdx.x * tile;
     uint32_t fe = 0, fi = 0;          // bit it: neuron first + it * blockDim + tid fired
+    unsigned long long indeg = 0;     // excitatory in-degree of the neurons that fired
 #pragma unroll
     for (int it = 0; it < kNeuronsPerThread; ++it) {
         const uint32_t i = first + it * blockDim.x + threadIdx.x;
@@ -195,14 +449,16 @@ __global__ void k_neuron(DevNet n, const int *t_now)
         n.hist[i] = h;
         if (fired) {
             n.last_spike[i] = t;
+            indeg += (unsigned long long)(n.rin_off[i + 1] - n.rin_off[i]);
             if (exc) fe |= 1u << it; else fi |= 1u << it;
         }
     }
     // block-wide exclusive prefix of the per-thread counts (exc, inh)
     __shared__ int s_w[2][32];
     __shared__ int s_base[3];
+    __shared__ bool s_last;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    int ce = __popc(fe), ci = __popc(fi);
+    const int ce = __popc(fe), ci = __popc(fi);
     int ie = ce, ii = ci;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -224,114 +480,56 @@ __global__ void k_neuron(DevNet n, const int *t_now)
         s_base[2] = (se + si) ? atomicAdd(&n.ctr->step_cnt[par][2], se + si) : 0;
     }
     __syncthreads();
-    if (!(fe | fi)) return;
-    int pe = s_base[0] + s_w[0][warp] + ie - ce;
-    int pi = s_base[1] + s_w[1][warp] + ii - ci;
-    // raster index: spikes kept so far + this block's place among this step's
-    // spikes (exc of the block first, then inh)
-    const int blk_e = s_w[0][nw - 1] + 0;  // not used when nw == 1 (see below)
-    (void)blk_e;
-    int32_t *ring = n.ring_ids + (size_t)(t % (int)n.D) * n.N;
-    const unsigned long long rbase = n.ctr->raster_total;
-    int pr = s_base[2] + (s_w[0][warp] + ie - ce) + (s_w[1][warp] + ii - ci);
+    if (fe | fi) {
+        int pe = s_base[0] + s_w[0][warp] + ie - ce;
+        int pi = s_base[1] + s_w[1][warp] + ii - ci;
+        int32_t *ring = n.ring_ids + (size_t)(t % (int)n.D) * n.N;
+        const unsigned long long rbase = n.ctr->raster_total;
+        int pr = s_base[2] + (s_w[0][warp] + ie - ce) + (s_w[1][warp] + ii - ci);
 #pragma unroll
-    for (int it = 0; it < kNeuronsPerThread; ++it) {
-        const uint32_t i = first + it * blockDim.x + threadIdx.x;
-        const bool e = (fe >> it) & 1u, q = (fi >> it) & 1u;
-        if (!(e || q)) continue;
-        if (e) ring[pe++] = (int32_t)i;
-        else ring[n.N - 1 - (pi++)] = (int32_t)i;
-        const unsigned long long r = rbase + (unsigned long long)(pr++);
-        if (r < n.raster_cap) n.raster_gid[r] = (int32_t)i;
+        for (int it = 0; it < kNeuronsPerThread; ++it) {
+            const uint32_t i = first + it * blockDim.x + threadIdx.x;
+            const bool e = (fe >> it) & 1u, q = (fi >> it) & 1u;
+            if (!(e || q)) continue;
+            if (e) ring[pe++] = (int32_t)i;
+            else ring[n.N - 1 - (pi++)] = (int32_t)i;
+            const unsigned long long r = rbase + (unsigned long long)(pr++);
+            if (r < n.raster_cap) n.raster_gid[r] = (int32_t)i;
+        }
     }
-}
-
-// ---------------------------------------------------------------------------
-// S4: LTP.  Warp per neuron that fired at t; lanes walk its incoming
-// excitatory synapses.  The nearest arrival of the source with
-// t_pre + d <= t is the lowest set bit k >= d of the source's 32-step history
-// (lag k - d), else its latest older spike last_old (lag t - last_old - d).
-// Block 0 also closes the step: ring counts of slot t % D, counters, raster
-// step offset, the next step's time stamp.
-// ---------------------------------------------------------------------------
-__global__ void k_ltp(DevNet n, const int *t_now, int *t_next)
-{
-    __shared__ int32_t s_lut[kLut];
-    const int t = *t_now;
-    const int par = t & 1;
-    const bool stdp = !(n.flags & SNN_STDP_OFF);
-    for (int i = threadIdx.x; i < kLut; i += blockDim.x) s_lut[i] = n.lut_p[i];
+    const unsigned long long bdeg = block_sum(indeg);
+    if (threadIdx.x == 0) {
+        if (bdeg) atomicAdd(&n.ctr->l_exc, bdeg);
+        __threadfence();
+        s_last = atomicAdd(&n.ctr->done_blocks, 1u) == gridDim.x - 1;
+    }
     __syncthreads();
-    const int ce = n.ctr->step_cnt[par][0], ci = n.ctr->step_cnt[par][1];
-    const int total = ce + ci;
-    const int32_t *ring = n.ring_ids + (size_t)(t % (int)n.D) * n.N;
-    const int lane = threadIdx.x & 31;
-    const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
-    unsigned long long visits = 0;
-    for (uint32_t item = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; item < (uint32_t)total;
-         item += warps) {
-        const int32_t post = (int)item < ce ? ring[item] : ring[n.N - 1 - ((int)item - ce)];
-        const int64_t lo = n.rin_off[post], hi = n.rin_off[post + 1];
-        visits += (unsigned long long)(hi - lo);
-        if (!stdp) continue;
-        for (int64_t e = lo + lane; e < hi; e += 32) {
-            const uint64_t r = n.rin[e];
-            const uint32_t pre = (uint32_t)r;
-            const uint32_t ord = (uint32_t)(r >> 32) & 0xffffu;
-            const uint32_t d = (uint32_t)(r >> 48);
-            const uint32_t recent = n.hist[pre] & (0xffffffffu << d);
-            const int lag = recent ? (__ffs(recent) - 1 - (int)d) : (t - n.last_old[pre] - (int)d);
-            if (lag < kLut) {
-                const int32_t a = s_lut[lag];
-                if (a) n.sd[row_base(n, pre) + ord] += a;
-            }
-        }
+    if (!s_last || threadIdx.x != 0) return;
+    // last block: every other block's counts and writes are complete
+    __threadfence();
+    DevCounters *c = n.ctr;
+    volatile int *sc = c->step_cnt[par];
+    const int te = sc[0], ti = sc[1];
+    const int total = te + ti;
+    const int slot = t % (int)n.D;
+    n.ring_cnt[2 * slot] = te;
+    n.ring_cnt[2 * slot + 1] = ti;
+    c->spikes += (unsigned long long)total;
+    const unsigned long long rt = c->raster_total;
+    const unsigned long long room = (n.raster_cap > rt) ? n.raster_cap - rt : 0ull;
+    const unsigned long long kept = (unsigned long long)total < room ? (unsigned long long)total : room;
+    if (kept < (unsigned long long)total) {
+        if (c->raster_dropped == 0) c->raster_first_drop_t = t;
+        c->raster_dropped += (unsigned long long)total - kept;
     }
-    if (lane != 0) visits = 0;
-    const unsigned long long bv = block_sum(visits);
-    if (threadIdx.x == 0 && bv) atomicAdd(&n.ctr->l_exc, bv);
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        DevCounters *c = n.ctr;
-        const int slot = t % (int)n.D;
-        n.ring_cnt[2 * slot] = ce;
-        n.ring_cnt[2 * slot + 1] = ci;
-        c->spikes += (unsigned long long)total;
-        const unsigned long long rt = c->raster_total;
-        const unsigned long long room = (n.raster_cap > rt) ? n.raster_cap - rt : 0ull;
-        const unsigned long long kept = (unsigned long long)total < room ? (unsigned long long)total : room;
-        if (kept < (unsigned long long)total) {
-            if (c->raster_dropped == 0) c->raster_first_drop_t = t;
-            c->raster_dropped += (unsigned long long)total - kept;
-        }
-        c->raster_total = rt + kept;
-        if (n.raster_step_off) n.raster_step_off[t + 1 - n.raster_t0] = (int64_t)(rt + kept);
-        c->step_cnt[par ^ 1][0] = 0;
-        c->step_cnt[par ^ 1][1] = 0;
-        c->step_cnt[par ^ 1][2] = 0;
-        *t_next = t + 1;
-    }
-}
-
-// ---------------------------------------------------------------------------
-// S5: long-term plasticity over the excitatory rows of column blockIdx.y
-// (rows c*npc .. c*npc+ne-1 are contiguous): w = clamp(w + bias + sd, 0,
-// wmax), sd = (sd * decay + 2^15) >> 16, int64 intermediates.
-// ---------------------------------------------------------------------------
-__global__ void k_deriv(DevNet n, uint32_t chunk)
-{
-    (void)chunk;
-    const uint32_t col = blockIdx.y;
-    const int64_t lo = row_base(n, col * n.npc);
-    const int64_t hi = n.uniform_m ? (int64_t)(col * n.npc + n.ne) * n.uniform_m
-                                   : n.row_off[col * n.npc + n.ne];
-    for (int64_t k = lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < hi;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t s = n.sd[k];
-        long long nw = (long long)n.w[k] + n.deriv_bias + s;
-        nw = nw < 0 ? 0 : (nw > n.wmax ? n.wmax : nw);
-        n.w[k] = (int32_t)nw;
-        n.sd[k] = (int32_t)(((long long)s * n.deriv_decay + 32768) >> 16);
-    }
+    c->raster_total = rt + kept;
+    if (n.raster_step_off) n.raster_step_off[t + 1 - n.raster_t0] = (int64_t)(rt + kept);
+    c->step_cnt[par ^ 1][0] = 0;
+    c->step_cnt[par ^ 1][1] = 0;
+    c->step_cnt[par ^ 1][2] = 0;
+    c->ltp_pending = t;
+    c->done_blocks = 0;
+    *t_next = t + 1;
 }
 
 }  // namespace snn

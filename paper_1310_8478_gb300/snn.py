@@ -63,16 +63,20 @@ class SnnLaunch(ctypes.Structure):
     _fields_ = [("deliver_block", ctypes.c_uint32), ("deliver_blocks_per_sm", ctypes.c_uint32),
                 ("neuron_block", ctypes.c_uint32), ("ltp_block", ctypes.c_uint32),
                 ("ltp_blocks_per_sm", ctypes.c_uint32), ("deriv_block", ctypes.c_uint32),
-                ("graph_steps", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("graph_steps", ctypes.c_uint32), ("dense_block", ctypes.c_uint32),
+                ("dense_rows", ctypes.c_uint32), ("dense_permille", ctypes.c_uint32)]
 
 
 class SnnProfile(ctypes.Structure):
-    _fields_ = [("launches", ctypes.c_int64 * 5), ("ms", ctypes.c_double * 5)]
+    _fields_ = [("launches", ctypes.c_int64 * 5), ("ms", ctypes.c_double * 5),
+                ("dense_steps", ctypes.c_int64), ("dense_deriv_steps", ctypes.c_int64),
+                ("dense_events", ctypes.c_int64), ("dense_exc_events", ctypes.c_int64),
+                ("dense_ltp_visits", ctypes.c_int64)]
 
 
 SPIKE_DTYPE = np.dtype([("t", np.int32), ("gid", np.int32)])
 STIM_DTYPE = np.dtype([("t", np.int32), ("gid", np.int32), ("q16", np.int32)])
-KERNELS = ("deliver", "neuron", "ltp", "deriv", "other")
+KERNELS = ("deliver", "neuron", "ltp", "deriv", "dense")
 
 # every function the header declares, with its ctypes signature
 _P = ctypes.POINTER
@@ -337,7 +341,7 @@ class Network:
     def get_launch(self) -> dict:
         L = SnnLaunch()
         _check(self._lib.snn_get_launch(self.h, ctypes.byref(L)), "snn_get_launch")
-        return {k: getattr(L, k) for k, _ in SnnLaunch._fields_ if k != "reserved"}
+        return {k: getattr(L, k) for k, _ in SnnLaunch._fields_}
 
     def set_profile(self, on: bool):
         _check(self._lib.snn_set_profile(self.h, int(bool(on))), "snn_set_profile")
@@ -345,7 +349,10 @@ class Network:
     def profile(self) -> dict:
         p = SnnProfile()
         _check(self._lib.snn_read_profile(self.h, ctypes.byref(p)), "snn_read_profile")
-        return {k: (int(p.launches[i]), float(p.ms[i])) for i, k in enumerate(KERNELS)}
+        out = {k: (int(p.launches[i]), float(p.ms[i])) for i, k in enumerate(KERNELS)}
+        for k in ("dense_steps", "dense_deriv_steps", "dense_events", "dense_exc_events", "dense_ltp_visits"):
+            out[k] = int(getattr(p, k))
+        return out
 
     # observables
     @property

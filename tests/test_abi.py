@@ -21,7 +21,7 @@ def declared_functions():
 
 
 def test_library_builds_and_exports_every_declared_symbol():
-    path = eng.build()
+    path = eng.build_engine()
     assert os.path.exists(path)
     lib = ctypes.CDLL(path)
     names = declared_functions()
@@ -41,7 +41,8 @@ def test_config_struct_layout_matches_header():
     assert c.a_plus_mv.offset == 56 and c.seed.offset == 112 and c.raster_capacity.offset == 128
     assert ctypes.sizeof(c) == 136
     assert ctypes.sizeof(snn.SnnCounters) == 64
-    assert ctypes.sizeof(snn.SnnLaunch) == 32
+    assert ctypes.sizeof(snn.SnnLaunch) == 40
+    assert ctypes.sizeof(snn.SnnProfile) == 120
 
 
 def _rc_build(cfg, budget=0):

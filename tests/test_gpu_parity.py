@@ -18,13 +18,21 @@ FORCE_Q16 = 300 * 65536
 @pytest.fixture(scope="module")
 def eng():
     import paper_1310_8478_gb300 as e
-    e.build()
+    e.build_engine()
     return e
 
 
-def gpu_net(eng, cfg, **kw):
+MODES = {"auto": None, "sparse": 1001, "dense": 1}
+
+
+def gpu_net(eng, cfg, mode="auto", **kw):
+    """mode: 'auto' (device picks per step), 'sparse' (event-driven kernels
+    only) or 'dense' (the dense synapse pass whenever any neuron fired)."""
     kw.setdefault("raster_capacity", 1 << 22)
-    return eng.Network(cfg, **kw)
+    n = eng.Network(cfg, **kw)
+    if MODES[mode] is not None:
+        n.set_launch(dense_permille=MODES[mode])
+    return n
 
 
 def assert_same_run(orc_sim, net, check_state=True):
@@ -71,52 +79,62 @@ def test_generated_network_equals_oracle(eng, orc, cfg):
 # ---------------------------------------------------------------------------
 # whole runs, bit-exact
 # ---------------------------------------------------------------------------
-def test_col1_m100_full_second_bitexact(eng, orc):
+@pytest.mark.parametrize("mode", ["auto", "sparse", "dense"])
+def test_col1_m100_full_second_bitexact(eng, orc, mode):
     cfg = workloads.workload("col1_m100")
     o = orc.Oracle(cfg)
     o.run(1000)
-    with gpu_net(eng, cfg) as n:
+    with gpu_net(eng, cfg, mode) as n:
         n.run(1000)
         assert_same_run(o, n)
         assert n.counters()["spikes"] > 1000
+        if mode == "dense":
+            assert n.profile()["dense_steps"] > 300
 
 
+@pytest.mark.parametrize("mode", ["auto", "sparse", "dense"])
 @pytest.mark.parametrize("gx,gy,m,T,seed", [
     (2, 2, 60, 1100, 31),        # ring members coincide on a 2x2 torus; crosses a derivative update
     (3, 3, 100, 1050, 32),
     (1, 1, 100, 2100, 33),       # two derivative updates
     (5, 3, 40, 1030, 34),        # ragged grid
 ])
-def test_small_grids_bitexact_across_derivative_updates(eng, orc, gx, gy, m, T, seed):
+def test_small_grids_bitexact_across_derivative_updates(eng, orc, gx, gy, m, T, seed, mode):
     cfg = workloads.custom(grid_x=gx, grid_y=gy, fanout=m,
                            pct_ring=(40, 30, 20, 10) if gx * gy > 1 else (100, 0, 0, 0), seed=seed)
     o = orc.Oracle(cfg)
     o.run(T)
-    with gpu_net(eng, cfg) as n:
+    with gpu_net(eng, cfg, mode) as n:
         n.run(T)
         assert_same_run(o, n)
 
 
-def test_grid8_m1125_onset_bitexact(eng, orc):
+@pytest.fixture(scope="module")
+def grid8_onset(orc):
     # the 8x8, M = 1125 workload over its first 32 ms: activity grows from the
     # thalamic drive to ~70 % of the neurons firing every step
-    cfg = workloads.workload("grid8_m1125")
-    o = orc.Oracle(cfg)
+    o = orc.Oracle(workloads.workload("grid8_m1125"))
     o.run(32)
-    with gpu_net(eng, cfg) as n:
+    return o
+
+
+@pytest.mark.parametrize("mode", ["auto", "sparse", "dense"])
+def test_grid8_m1125_onset_bitexact(eng, grid8_onset, mode):
+    with gpu_net(eng, workloads.workload("grid8_m1125"), mode) as n:
         n.run(32)
-        assert_same_run(o, n)
+        assert_same_run(grid8_onset, n)
         assert n.counters()["spikes"] > 100000
 
 
+@pytest.mark.parametrize("mode", ["sparse", "dense"])
 @pytest.mark.parametrize("flag_pair", [("STDP_OFF", 1, 1), ("DELIVERY_OFF", 2, 2)])
-def test_debug_flags_bitexact(eng, orc, flag_pair):
+def test_debug_flags_bitexact(eng, orc, flag_pair, mode):
     _, of, gf = flag_pair
     cfg = workloads.custom(grid_x=2, grid_y=1, fanout=100, pct_ring=(40, 30, 20, 10), seed=41, flags=gf)
     o = orc.Oracle(cfg, flags=of)
-    o.run(600)
-    with gpu_net(eng, cfg) as n:
-        n.run(600)
+    o.run(1200)
+    with gpu_net(eng, cfg, mode) as n:
+        n.run(1200)
         assert_same_run(o, n)
 
 
@@ -179,9 +197,11 @@ SHAPES = [
     dict(deliver_block=256, deliver_blocks_per_sm=8, neuron_block=256, ltp_block=256, ltp_blocks_per_sm=8,
          graph_steps=50),
     dict(deliver_block=64, deliver_blocks_per_sm=1, neuron_block=32, ltp_block=32, ltp_blocks_per_sm=1,
-         graph_steps=1),
+         graph_steps=1, dense_permille=1001),
     dict(deliver_block=1024, deliver_blocks_per_sm=3, neuron_block=1024, ltp_block=512, ltp_blocks_per_sm=5,
-         graph_steps=20, deriv_block=64),
+         graph_steps=20, deriv_block=64, dense_permille=1, dense_block=128, dense_rows=37),
+    dict(graph_steps=10, dense_permille=1, dense_block=512, dense_rows=1250),
+    dict(graph_steps=2, dense_permille=20, dense_block=32, dense_rows=1),
 ]
 
 
@@ -214,16 +234,17 @@ def test_step_by_step_equals_run(eng):
 # ---------------------------------------------------------------------------
 # checkpoint / resume, host end-to-end call
 # ---------------------------------------------------------------------------
-def test_checkpoint_resume_is_bitexact(eng):
+@pytest.mark.parametrize("mode", ["auto", "dense"])
+def test_checkpoint_resume_is_bitexact(eng, mode):
     cfg = workloads.custom(grid_x=2, grid_y=2, fanout=100, pct_ring=(40, 30, 20, 10), seed=61)
-    with gpu_net(eng, cfg) as a:
+    with gpu_net(eng, cfg, mode) as a:
         a.run(1200)
         ref_r = a.raster(600, 1200)
         ref_w = a.weights()
-    with gpu_net(eng, cfg) as b:
+    with gpu_net(eng, cfg, mode) as b:
         b.run(600)
         blob = b.save_state()
-    with gpu_net(eng, cfg) as c:
+    with gpu_net(eng, cfg, mode) as c:
         c.load_state(blob)
         assert c.counters()["t"] == 600
         c.run(600)
@@ -235,7 +256,7 @@ def test_checkpoint_resume_is_bitexact(eng):
 
 def test_run_host_equals_run_and_raster(eng):
     cfg = workloads.custom(grid_x=2, grid_y=2, fanout=100, pct_ring=(40, 30, 20, 10), seed=62)
-    with gpu_net(eng, cfg) as a, gpu_net(eng, cfg) as b:
+    with gpu_net(eng, cfg) as a, gpu_net(eng, cfg, "dense") as b:
         a.run(300)
         ref = a.raster(0, 300)
         t1, g1 = b.run_host(150)
@@ -260,3 +281,31 @@ def test_raster_capacity_overflow_is_reported(eng):
         with pytest.raises(eng.SnnError) as e:
             n.raster(0, 400)
         assert e.value.code == -6
+
+
+def test_host_thalamic_events_reproduce_the_internal_drive(eng):
+    # the drive drawn on the host and fed as external stimulus, with the
+    # net's own draws switched off, gives the same run
+    cfg = workloads.custom(grid_x=3, grid_y=2, fanout=150, pct_ring=(40, 30, 20, 10), seed=63)
+    from paper_1310_8478_gb300 import snn
+    with gpu_net(eng, cfg) as a, gpu_net(eng, cfg) as b:
+        a.run(400)
+        b.set_thalamic(False)
+        ev = snn.snn_thalamic_events(cfg, 0, 400)
+        for k in range(4):
+            b.run_host_counts(100, ev[k * 600:(k + 1) * 600])
+        ra, rb = a.raster(), b.raster()
+        assert np.array_equal(ra[0], rb[0]) and np.array_equal(ra[1], rb[1])
+        wa, wb = a.weights(), b.weights()
+        assert np.array_equal(wa[0], wb[0]) and np.array_equal(wa[1], wb[1])
+
+
+def test_reset_restarts_the_same_run(eng):
+    cfg = workloads.custom(grid_x=2, grid_y=2, fanout=100, pct_ring=(40, 30, 20, 10), seed=64)
+    with gpu_net(eng, cfg) as n:
+        n.run(1100)
+        r1, w1 = n.raster(), n.weights()
+        n.reset()
+        n.run(1100)
+        r2, w2 = n.raster(), n.weights()
+        assert np.array_equal(r1[1], r2[1]) and np.array_equal(w1[1], w2[1])
