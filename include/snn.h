@@ -236,6 +236,29 @@ int snn_read_synapses(snn_net *net, uint32_t first, uint32_t count, int32_t *hos
                       uint8_t *host_delay, int32_t *host_w, int32_t *host_sd, size_t cap,
                       size_t *n_out);
 
+/*
+ * snn_read_synapses_noalloc -- snn_read_synapses without any device
+ * allocation.  The paper has no counterpart; it serves callers that cannot
+ * allocate device memory once networks are running: a serving loop that has
+ * committed its whole HBM budget to resident networks, code that must not
+ * pay the device-wide synchronization of cudaMalloc / cudaFree while other
+ * networks' steps are in flight on other streams, or hosts whose device
+ * memory belongs to a framework allocator they cannot reach from here.
+ * The device staging is a fixed array compiled into the library
+ * (SNN_NOALLOC_MAX_SYNAPSES synapses, about 13 MiB, held by every GPU that
+ * loads the library until the process exits).  A range with more synapses
+ * is rejected with SNN_EINVAL; split it.  The first call on a device looks
+ * up the array's device address with that device current, so make it before
+ * any stream capture.  Every call shares the array: calls that overlap on
+ * the GPU (different threads, different nets on the same device) race, so
+ * serialize them.  Arguments, results and errors otherwise as
+ * snn_read_synapses.
+ */
+#define SNN_NOALLOC_MAX_SYNAPSES (1u << 20)
+int snn_read_synapses_noalloc(snn_net *net, uint32_t first, uint32_t count, int32_t *host_tgt,
+                              uint8_t *host_delay, int32_t *host_w, int32_t *host_sd, size_t cap,
+                              size_t *n_out);
+
 /* snn_read_weights -- w and sd of every synapse, canonical order (cap >= synapses). */
 int snn_read_weights(snn_net *net, int32_t *host_w, int32_t *host_sd, size_t cap, size_t *n_out);
 

@@ -9,6 +9,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -50,6 +51,16 @@ void *g_alloc_ctx = nullptr;
     } while (0)
 
 constexpr uint32_t kStateMagic = 0x534e4e31u;  // "SNN1"
+
+// Device staging of snn_read_synapses_noalloc: target, weight and sd words,
+// then the delay bytes, for SNN_NOALLOC_MAX_SYNAPSES synapses.  Host code
+// must not use this name as an address: it looks the address up per device.
+constexpr size_t kNoAllocWords = (size_t)SNN_NOALLOC_MAX_SYNAPSES * 3 + SNN_NOALLOC_MAX_SYNAPSES / 4;
+static __device__ __align__(256) int32_t g_noalloc_scratch[kNoAllocWords];
+
+constexpr int kMaxDevices = 64;
+int32_t *g_noalloc_ptr[kMaxDevices] = {nullptr};
+std::mutex g_noalloc_mutex;
 
 __global__ void k_fill_row_off(int64_t *row_off, uint32_t n, uint32_t m)
 {
@@ -1167,6 +1178,62 @@ int snn_read_synapses(snn_net *net, uint32_t first, uint32_t count, int32_t *hos
         }
         r0 = r1;
     }
+    return SNN_OK;
+}
+
+int snn_read_synapses_noalloc(snn_net *net, uint32_t first, uint32_t count, int32_t *host_tgt, uint8_t *host_delay,
+                              int32_t *host_w, int32_t *host_sd, size_t cap, size_t *n_out)
+{
+    if (!net) { set_error("net is NULL"); return SNN_EINVAL; }
+    if ((uint64_t)first + count > net->N) { set_error("row range out of bounds"); return SNN_EINVAL; }
+    int64_t a = 0, b = 0;
+    SNN_CUDA(cudaMemcpyAsync(&a, net->row_off + first, 8, cudaMemcpyDeviceToHost, net->stream));
+    SNN_CUDA(cudaMemcpyAsync(&b, net->row_off + first + count, 8, cudaMemcpyDeviceToHost, net->stream));
+    SNN_CUDA(cudaStreamSynchronize(net->stream));
+    const int64_t total = b - a;
+    if (n_out) *n_out = (size_t)total;
+    if ((size_t)total > cap) { set_error("need %lld entries", (long long)total); return SNN_ETRUNC; }
+    if (total > (int64_t)SNN_NOALLOC_MAX_SYNAPSES) {
+        set_error("range holds %lld synapses, more than the %u the no-allocation read can stage; split it",
+                  (long long)total, (unsigned)SNN_NOALLOC_MAX_SYNAPSES);
+        return SNN_EINVAL;
+    }
+    if (total == 0) return SNN_OK;
+    // device address of the staging array, once per device, with that device current
+    if (net->device < 0 || net->device >= kMaxDevices) { set_error("device ordinal too large"); return SNN_EINVAL; }
+    int32_t *base = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        if (!g_noalloc_ptr[net->device]) {
+            int prev = 0;
+            SNN_CUDA(cudaGetDevice(&prev));
+            if (prev != net->device) SNN_CUDA(cudaSetDevice(net->device));
+            void *ptr = nullptr;
+            const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+            if (prev != net->device) cudaSetDevice(prev);
+            if (e != cudaSuccess) {
+                set_error("cudaGetSymbolAddress of the staging array failed: %s", cudaGetErrorString(e));
+                return SNN_ECUDA;
+            }
+            g_noalloc_ptr[net->device] = (int32_t *)ptr;
+        }
+        base = g_noalloc_ptr[net->device];
+    }
+    SNN_TRY(flush_owed(net));
+    const size_t M = SNN_NOALLOC_MAX_SYNAPSES;
+    int32_t *dt = host_tgt ? base : nullptr;
+    int32_t *dw = host_w ? base + M : nullptr;
+    int32_t *ds = host_sd ? base + 2 * M : nullptr;
+    uint8_t *dd = host_delay ? reinterpret_cast<uint8_t *>(base + 3 * M) : nullptr;
+    // every staged entry of the range is written by the kernel: nothing to clear
+    k_read_rows<<<grid_for(net, 8), 128, 0, net->stream>>>(net->dn, net->gen, net->canon_delay, first, count, a,
+                                                           dt, dd, dw, ds);
+    SNN_CUDA(cudaGetLastError());
+    if (dt) SNN_CUDA(cudaMemcpyAsync(host_tgt, dt, (size_t)total * 4, cudaMemcpyDeviceToHost, net->stream));
+    if (dd) SNN_CUDA(cudaMemcpyAsync(host_delay, dd, (size_t)total, cudaMemcpyDeviceToHost, net->stream));
+    if (dw) SNN_CUDA(cudaMemcpyAsync(host_w, dw, (size_t)total * 4, cudaMemcpyDeviceToHost, net->stream));
+    if (ds) SNN_CUDA(cudaMemcpyAsync(host_sd, ds, (size_t)total * 4, cudaMemcpyDeviceToHost, net->stream));
+    SNN_CUDA(cudaStreamSynchronize(net->stream));
     return SNN_OK;
 }
 

@@ -21,6 +21,7 @@ STDP_OFF = 1
 DELIVERY_OFF = 2
 
 OK, EINVAL, ENOMEM, ECUDA, EOVERFLOW, ETIMEOUT, ETRUNC, ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
+SNN_NOALLOC_MAX_SYNAPSES = 1 << 20   # staging size of snn_read_synapses_noalloc
 
 
 class SnnConfig(ctypes.Structure):
@@ -98,6 +99,8 @@ _SIGS = {
     "snn_raster_reset": (ctypes.c_int, [_vp]),
     "snn_read_synapses": (ctypes.c_int, [_vp, ctypes.c_uint32, ctypes.c_uint32, _vp, _vp, _vp, _vp,
                                          ctypes.c_size_t, _P(ctypes.c_size_t)]),
+    "snn_read_synapses_noalloc": (ctypes.c_int, [_vp, ctypes.c_uint32, ctypes.c_uint32, _vp, _vp, _vp, _vp,
+                                                 ctypes.c_size_t, _P(ctypes.c_size_t)]),
     "snn_read_weights": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_size_t, _P(ctypes.c_size_t)]),
     "snn_read_neurons": (ctypes.c_int, [_vp, ctypes.c_uint32, ctypes.c_uint32, _vp, _vp]),
     "snn_read_counters": (ctypes.c_int, [_vp, _P(SnnCounters)]),
