@@ -338,7 +338,7 @@ int alloc_common(snn_net *net)
     dn.seed_hi = (uint32_t)(net->cfg.seed >> 32);
     dn.flags = net->cfg.flags;
     dn.deriv_period = net->cfg.deriv_period_ms;
-    dn.dense_rows = net->launch.dense_rows;
+    dn.dense_rows = net->launch.dense_rows ? net->launch.dense_rows : 64;
     dn.dense_min_spikes = dense_threshold(net->N, net->launch.dense_permille);
     dn.deriv_bias = net->cfg.deriv_bias_q16;
     dn.deriv_decay = net->cfg.deriv_decay_q16;
@@ -356,6 +356,20 @@ int setup_dense(snn_net *net)
     SNN_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, net->device));
     if (bytes + 1024 > (size_t)optin) return SNN_OK;
     SNN_CUDA(cudaFuncSetAttribute(k_dense, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    int per_sm = 0;
+    SNN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dense, (int)net->launch.dense_block, bytes));
+    if (per_sm < 1) return SNN_OK;
+    // rows per block: the launch's value, or (0) enough blocks for about 16
+    // waves of resident blocks, with at least 64 rows to pay for the staging
+    uint32_t rows = net->launch.dense_rows;
+    if (rows == 0) {
+        const uint32_t npc = net->cfg.neurons_per_col, C = net->dn.C;
+        const uint64_t want = 16ull * per_sm * net->sm_count;
+        uint32_t chunks = (uint32_t)std::max<uint64_t>(1, (want + C - 1) / C);
+        chunks = std::min(chunks, std::max(1u, npc / 64));
+        rows = (npc + chunks - 1) / chunks;
+    }
+    net->dn.dense_rows = rows;
     net->dense_ok = true;
     return SNN_OK;
 }
@@ -459,7 +473,7 @@ int start_net(const snn_config *cfg, void *cuda_stream, size_t budget, snn_net *
     net->launch.deriv_block = 256;
     net->launch.graph_steps = 50;
     net->launch.dense_block = 512;
-    net->launch.dense_rows = 250;
+    net->launch.dense_rows = 0;
     net->launch.dense_permille = 50;
     (void)cuda_stream;
     return SNN_OK;
@@ -557,7 +571,7 @@ void launch_step(snn_net *net, int32_t t)
     k_deliver<<<grid_for(net, L.deliver_blocks_per_sm), L.deliver_block, 0, s>>>(dn, t_now);
     mark(0);
     if (net->dense_ok) {
-        const uint32_t chunks = (dn.npc + L.dense_rows - 1) / L.dense_rows;
+        const uint32_t chunks = (dn.npc + dn.dense_rows - 1) / dn.dense_rows;
         mark(4);
         k_dense<<<dn.C * chunks, L.dense_block, dense_smem_bytes(dn.npc, L.dense_block), s>>>(dn, t_now);
         mark(4);
@@ -1007,7 +1021,6 @@ int snn_set_launch(snn_net *net, const snn_launch *launch)
     }
     if (L.deliver_blocks_per_sm > 64 || L.ltp_blocks_per_sm > 64) { set_error("blocks per SM must be <= 64"); return SNN_EINVAL; }
     net->launch = L;
-    net->dn.dense_rows = L.dense_rows;
     net->dn.dense_min_spikes = dense_threshold(net->N, L.dense_permille);
     SNN_TRY(setup_dense(net));
     if (!net->dense_ok) net->dn.dense_min_spikes = 0xffffffffu;

@@ -19,6 +19,7 @@ constexpr int kSlotStride = 16;      // entries per column in the neighbour tabl
 constexpr int32_t kNoPending = -(1 << 30);  // ltp_pending value when no LTP is owed
 constexpr uint32_t kMaxCompactNpc = 4096;    // 12-bit local ids in the compact target format
 constexpr uint32_t kDenseMaxNpc = 3200;      // staged columns must fit in shared memory
+constexpr int kUnroll = 4;                   // dense pass: positions per lane in flight
 
 // Device counters and per-step bookkeeping (one struct, device memory).
 struct DevCounters {

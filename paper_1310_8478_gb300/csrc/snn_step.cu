@@ -321,40 +321,62 @@ __global__ void __launch_bounds__(512) k_dense(DevNet n, const int *t_now)
         if (busy) {
             const int m = off[D];
             const int64_t base = row_base(n, p);
+            const uint16_t *rt = n.tgt16 + base;
+            int32_t *rw = n.w + base;
+            int32_t *rs = n.sd + base;
             int d = 1;
-            for (int k = lane; k < m; k += 32) {
-                while (k >= w_off[d]) ++d;
-                const uint32_t f = w_flag[d];
-                const int32_t a = w_amt[d];
-                if (!exc) {
-                    if (f) {
-                        const uint32_t v = n.tgt16[base + k];
-                        atomicAdd(&s_in[(v >> 12) * npc + (v & 0xfffu)], n.w[base + k]);
+            // kUnroll positions per lane: the target, weight and sd loads of all
+            // of them are issued before any is used
+            for (int k0 = lane; k0 < m; k0 += 32 * kUnroll) {
+                uint32_t v[kUnroll];
+                int32_t sv[kUnroll], wv[kUnroll], am[kUnroll];
+                bool fl[kUnroll], act[kUnroll];
+#pragma unroll
+                for (int u = 0; u < kUnroll; ++u) {
+                    const int k = k0 + 32 * u;
+                    fl[u] = false;
+                    am[u] = 0;
+                    act[u] = false;
+                    v[u] = 0;
+                    sv[u] = 0;
+                    wv[u] = 0;
+                    if (k < m) {
+                        while (k >= w_off[d]) ++d;
+                        fl[u] = w_flag[d] != 0;
+                        am[u] = w_amt[d];
+                        act[u] = fl[u] || (exc && (am[u] || deriv_on));
+                        if (act[u]) {
+                            v[u] = rt[k];
+                            if (exc) sv[u] = rs[k];
+                            if (fl[u] || (exc && deriv_on)) wv[u] = rw[k];
+                        }
                     }
-                    continue;
                 }
-                if (!f && !a && !deriv_on) continue;
-                const int64_t pos = base + k;
-                const uint32_t v = n.tgt16[pos];
-                const uint32_t idx = (v >> 12) * npc + (v & 0xfffu);
-                const int lag = s_lag[idx];
-                const bool pot = a && lag == 1;
-                const int32_t dep = (f && stdp) ? s_lutm[lag] : 0;
-                if (!pot && !deriv_on && !f) continue;
-                if (ltp_on && lag == 1) visits++;
-                int32_t s = (pot || deriv_on || dep) ? n.sd[pos] : 0;
-                if (pot) s += a;
-                int32_t wv = 0;
-                if (deriv_on) {
-                    wv = deriv_w(n, n.w[pos], s);
-                    s = deriv_sd(n, s);
-                    n.w[pos] = wv;
-                } else if (f) {
-                    wv = n.w[pos];
+#pragma unroll
+                for (int u = 0; u < kUnroll; ++u) {
+                    if (!act[u]) continue;
+                    const int k = k0 + 32 * u;
+                    const uint32_t idx = (v[u] >> 12) * npc + (v[u] & 0xfffu);
+                    if (!exc) {
+                        atomicAdd(&s_in[idx], wv[u]);
+                        continue;
+                    }
+                    const int lag = s_lag[idx];
+                    const bool pot = am[u] && lag == 1;
+                    const int32_t dep = (fl[u] && stdp) ? s_lutm[lag] : 0;
+                    if (ltp_on && lag == 1) visits++;
+                    int32_t sdv = sv[u];
+                    if (pot) sdv += am[u];
+                    int32_t w_new = wv[u];
+                    if (deriv_on) {
+                        w_new = deriv_w(n, wv[u], sdv);
+                        sdv = deriv_sd(n, sdv);
+                        rw[k] = w_new;
+                    }
+                    if (fl[u]) atomicAdd(&s_in[idx], w_new);
+                    sdv -= dep;
+                    if (pot || deriv_on || dep) rs[k] = sdv;
                 }
-                if (f) atomicAdd(&s_in[idx], wv);
-                s -= dep;
-                if (pot || deriv_on || dep) n.sd[pos] = s;
             }
         }
         __syncwarp();
