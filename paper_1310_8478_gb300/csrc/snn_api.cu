@@ -85,7 +85,8 @@ struct snn_net {
     GenParams gen{};
     DevNet dn{};
     uint32_t N = 0;
-    int64_t S = 0;
+    int64_t S = 0;                  // synapses
+    int64_t S_store = 0;            // stored slots (generated rows padded to the stride)
     int64_t n_rin = 0;
     size_t budget = 0;
     size_t bytes_held = 0;
@@ -279,8 +280,8 @@ int alloc_common(snn_net *net)
     const uint32_t D = net->cfg.max_delay_ms;
     DevNet &dn = net->dn;
     const bool compact = !net->explicit_net && net->cfg.neurons_per_col <= kMaxCompactNpc;
-    if (compact) SNN_TRY(dalloc_t(net, (size_t)net->S, &net->tgt16));
-    else SNN_TRY(dalloc_t(net, (size_t)net->S, &net->tgt));
+    if (compact) SNN_TRY(dalloc_t(net, (size_t)net->S_store, &net->tgt16));
+    else SNN_TRY(dalloc_t(net, (size_t)net->S_store, &net->tgt));
     const uint32_t C = net->cfg.grid_x * net->cfg.grid_y;
     SNN_TRY(dalloc_t(net, (size_t)C * kSlotStride, &net->nbr));
     {
@@ -291,8 +292,8 @@ int alloc_common(snn_net *net)
                     (int32_t)(sl < (uint32_t)kSlots ? slot_column(c, sl, net->cfg.grid_x, net->cfg.grid_y) : c);
         SNN_CUDA(cudaMemcpy(net->nbr, nb.data(), nb.size() * 4, cudaMemcpyHostToDevice));
     }
-    SNN_TRY(dalloc_t(net, (size_t)net->S, &net->w));
-    SNN_TRY(dalloc_t(net, (size_t)net->S, &net->sd));
+    SNN_TRY(dalloc_t(net, (size_t)net->S_store, &net->w));
+    SNN_TRY(dalloc_t(net, (size_t)net->S_store, &net->sd));
     SNN_TRY(dalloc_t(net, (size_t)N * kDoffStride, &net->doff));
     SNN_TRY(dalloc_t(net, (size_t)N + 1, &net->row_off));
     SNN_TRY(dalloc_t(net, (size_t)N + 1, &net->rin_off));
@@ -317,7 +318,7 @@ int alloc_common(snn_net *net)
     dn.C = net->cfg.grid_x * net->cfg.grid_y;
     dn.D = D;
     dn.D_inh = 1;
-    dn.S = net->S;
+    dn.S = net->S_store;
     dn.row_off = net->row_off;
     dn.doff = net->doff;
     dn.tgt = net->tgt;
@@ -526,7 +527,7 @@ int deriv_grid_x(const snn_net *net)
 {
     const DevNet &dn = net->dn;
     const int64_t per_col = dn.uniform_m ? (int64_t)dn.ne * dn.uniform_m
-                                         : net->S / std::max<uint32_t>(1u, dn.C) + 1;
+                                         : net->S_store / std::max<uint32_t>(1u, dn.C) + 1;
     return (int)std::min<int64_t>(1024, std::max<int64_t>(1, per_col / ((int64_t)net->launch.deriv_block * 4)));
 }
 
@@ -683,6 +684,18 @@ int run_steps(snn_net *net, uint32_t n_ms)
         }
     }
     return finish_run(net);
+}
+
+// canonical (unpadded, source-major) index of the first synapse of row p
+int canon_offset(snn_net *net, uint32_t p, int64_t *out)
+{
+    if (net->dn.uniform_m) {
+        *out = (int64_t)p * net->dn.canon_m;
+        return SNN_OK;
+    }
+    SNN_CUDA(cudaMemcpyAsync(out, net->row_off + p, 8, cudaMemcpyDeviceToHost, net->stream));
+    SNN_CUDA(cudaStreamSynchronize(net->stream));
+    return SNN_OK;
 }
 
 // apply the LTP / long-term update owed by the last step (before reads)
@@ -857,20 +870,25 @@ int snn_build_network(const snn_config *cfg, void *cuda_stream, size_t hbm_budge
     if (r != SNN_OK) return fail(r);
     const snn_config &c = net->cfg;
     net->S = (int64_t)net->N * c.fanout;
+    const bool compact = c.neurons_per_col <= kMaxCompactNpc;
+    const uint32_t m_store = compact ? ((c.fanout + 7u) & ~7u) : c.fanout;
+    net->S_store = (int64_t)net->N * m_store;
     const int64_t n_rin_est = (int64_t)c.grid_x * c.grid_y * c.exc_per_col * c.fanout;
-    const size_t need = footprint(&c, net->N, net->S, n_rin_est, false) + (size_t)c.raster_capacity * 4 + (1 << 17);
+    const size_t need = footprint(&c, net->N, net->S_store, n_rin_est, false) + (size_t)c.raster_capacity * 4 + (1 << 17);
     if (hbm_budget_bytes && need > hbm_budget_bytes) {
         set_error("network needs about %zu bytes, budget is %zu", need, hbm_budget_bytes);
         return fail(SNN_ENOMEM);
     }
     if ((r = cuda_init(net, cuda_stream)) != SNN_OK) return fail(r);
     if ((r = alloc_common(net)) != SNN_OK) return fail(r);
-    net->dn.uniform_m = c.fanout;
+    net->dn.uniform_m = m_store;
+    net->dn.canon_m = c.fanout;
     net->wrange = WeightRange{c.w_exc0_q16, c.w_exc0_q16, c.w_inh0_q16, c.w_inh0_q16};
     GenParams &g = net->gen;
     g.npc = c.neurons_per_col;
     g.ne = c.exc_per_col;
     g.m = c.fanout;
+    g.m_store = m_store;
     g.D = c.max_delay_ms;
     g.gx = c.grid_x;
     g.gy = c.grid_y;
@@ -884,7 +902,7 @@ int snn_build_network(const snn_config *cfg, void *cuda_stream, size_t hbm_budge
     g.w_exc0 = c.w_exc0_q16;
     g.w_inh0 = c.w_inh0_q16;
     const int gr = grid_for(net, 16);
-    k_fill_row_off<<<gr, 256, 0, net->stream>>>(net->row_off, net->N, c.fanout);
+    k_fill_row_off<<<gr, 256, 0, net->stream>>>(net->row_off, net->N, m_store);
     k_gen_rows<<<gr, 256, 0, net->stream>>>(g, net->N, net->doff, net->tgt, net->tgt16, net->w, net->sd);
     if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(net->stream) != cudaSuccess) {
         set_error("network generation failed: %s", cudaGetErrorString(cudaGetLastError()));
@@ -921,6 +939,7 @@ int snn_build_network_explicit(const snn_config *cfg, const int64_t *host_row_of
     }
     net->explicit_net = true;
     net->S = S;
+    net->S_store = S;
     int64_t n_exc = 0;
     net->wrange = WeightRange{0, 0, 0, 0};
     for (uint32_t p = 0; p < N; ++p) {
@@ -1148,10 +1167,9 @@ int snn_read_synapses(snn_net *net, uint32_t first, uint32_t count, int32_t *hos
     if (!net) { set_error("net is NULL"); return SNN_EINVAL; }
     if ((uint64_t)first + count > net->N) { set_error("row range out of bounds"); return SNN_EINVAL; }
     SNN_TRY(flush_owed(net));
-    std::vector<int64_t> ro(2);
-    SNN_CUDA(cudaMemcpyAsync(&ro[0], net->row_off + first, 8, cudaMemcpyDeviceToHost, net->stream));
-    SNN_CUDA(cudaMemcpyAsync(&ro[1], net->row_off + first + count, 8, cudaMemcpyDeviceToHost, net->stream));
-    SNN_CUDA(cudaStreamSynchronize(net->stream));
+    int64_t ro[2];
+    SNN_TRY(canon_offset(net, first, &ro[0]));
+    SNN_TRY(canon_offset(net, first + count, &ro[1]));
     const int64_t total = ro[1] - ro[0];
     if (n_out) *n_out = (size_t)total;
     if ((size_t)total > cap) { set_error("need %lld entries", (long long)total); return SNN_ETRUNC; }
@@ -1159,14 +1177,12 @@ int snn_read_synapses(snn_net *net, uint32_t first, uint32_t count, int32_t *hos
     // chunks of rows of at most ~64 M synapses through device scratch
     const int64_t chunk_syn = 64ll << 20;
     uint32_t r0 = first;
-    std::vector<int64_t> offs;
     while (r0 < first + count) {
         // find r1 with row_off[r1] - row_off[r0] <= chunk_syn (rows hold <= 65535)
         uint32_t r1 = std::min<uint32_t>(first + count, r0 + (uint32_t)std::max<int64_t>(1, chunk_syn / 65536));
         int64_t a = 0, b = 0;
-        SNN_CUDA(cudaMemcpyAsync(&a, net->row_off + r0, 8, cudaMemcpyDeviceToHost, net->stream));
-        SNN_CUDA(cudaMemcpyAsync(&b, net->row_off + r1, 8, cudaMemcpyDeviceToHost, net->stream));
-        SNN_CUDA(cudaStreamSynchronize(net->stream));
+        SNN_TRY(canon_offset(net, r0, &a));
+        SNN_TRY(canon_offset(net, r1, &b));
         const int64_t n = b - a;
         if (n > 0) {
             int32_t *dt = nullptr, *dw = nullptr, *ds = nullptr;
@@ -1200,9 +1216,8 @@ int snn_read_synapses_noalloc(snn_net *net, uint32_t first, uint32_t count, int3
     if (!net) { set_error("net is NULL"); return SNN_EINVAL; }
     if ((uint64_t)first + count > net->N) { set_error("row range out of bounds"); return SNN_EINVAL; }
     int64_t a = 0, b = 0;
-    SNN_CUDA(cudaMemcpyAsync(&a, net->row_off + first, 8, cudaMemcpyDeviceToHost, net->stream));
-    SNN_CUDA(cudaMemcpyAsync(&b, net->row_off + first + count, 8, cudaMemcpyDeviceToHost, net->stream));
-    SNN_CUDA(cudaStreamSynchronize(net->stream));
+    SNN_TRY(canon_offset(net, first, &a));
+    SNN_TRY(canon_offset(net, first + count, &b));
     const int64_t total = b - a;
     if (n_out) *n_out = (size_t)total;
     if ((size_t)total > cap) { set_error("need %lld entries", (long long)total); return SNN_ETRUNC; }
@@ -1330,7 +1345,7 @@ struct StateHeader {
 int snn_save_state(snn_net *net, void *host_buf, size_t cap, size_t *n)
 {
     if (!net || !n) { set_error("NULL argument"); return SNN_EINVAL; }
-    const size_t N = net->N, D = net->cfg.max_delay_ms, S = (size_t)net->S;
+    const size_t N = net->N, D = net->cfg.max_delay_ms, S = (size_t)net->S_store;
     const size_t need = sizeof(StateHeader) + N * 24 + D * N * 4 + D * 8 + S * 8 + sizeof(DevCounters);
     *n = need;
     if (!host_buf) return SNN_OK;
@@ -1363,7 +1378,7 @@ int snn_save_state(snn_net *net, void *host_buf, size_t cap, size_t *n)
 int snn_load_state(snn_net *net, const void *host_buf, size_t n)
 {
     if (!net || !host_buf) { set_error("NULL argument"); return SNN_EINVAL; }
-    const size_t N = net->N, D = net->cfg.max_delay_ms, S = (size_t)net->S;
+    const size_t N = net->N, D = net->cfg.max_delay_ms, S = (size_t)net->S_store;
     const size_t need = sizeof(StateHeader) + N * 24 + D * N * 4 + D * 8 + S * 8 + sizeof(DevCounters);
     if (n < need) { set_error("checkpoint is %zu bytes, need %zu", n, need); return SNN_EINVAL; }
     StateHeader h{};

@@ -25,8 +25,14 @@ __global__ void k_gen_rows(GenParams g, uint32_t n_rows, uint16_t *doff, int32_t
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned lt = lanemask_lt();
     for (uint32_t p = blockIdx.x * kWarps + warp; p < n_rows; p += gridDim.x * kWarps) {
-        const int64_t base = (int64_t)p * g.m;
+        const int64_t base = (int64_t)p * g.m_store;
         const bool exc = (p % g.npc) < g.ne;
+        for (uint32_t j = g.m + lane; j < g.m_store; j += 32) {   // padding tail
+            if (tgt16) tgt16[base + j] = 0;
+            else tgt[base + j] = 0;
+            w[base + j] = 0;
+            sd[base + j] = 0;
+        }
         s_cnt[warp][lane] = 0;
         __syncwarp();
         for (uint32_t j = lane; j < g.m; j += 32) {
@@ -78,7 +84,7 @@ __global__ void k_count_indeg(DevNet n, int32_t *indeg_exc, int32_t *indeg_inh)
         const bool exc = (p % n.npc) < n.ne;
         int32_t *deg = exc ? indeg_exc : indeg_inh;
         const uint32_t col = p / n.npc;
-        const int64_t lo = n.row_off[p], hi = n.row_off[p + 1];
+        const int64_t lo = row_base(n, p), hi = lo + row_len(n, p);
         for (int64_t k = lo + lane; k < hi; k += 32) atomicAdd(&deg[target_gid(n, col, k)], 1);
     }
 }
@@ -241,21 +247,21 @@ __global__ void k_read_rows(DevNet n, GenParams g, const uint8_t *canon_delay, u
 {
     for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < count; r += gridDim.x * blockDim.x) {
         const uint32_t p = first + r;
-        const int64_t lo = n.row_off[p], hi = n.row_off[p + 1];
+        const int64_t lo = row_base(n, p), len = row_len(n, p), cb = canon_base(n, p);
         const uint16_t *off = n.doff + (size_t)p * kDoffStride;
         uint16_t used[kDoffStride];
         for (int d = 0; d < kDoffStride; ++d) used[d] = 0;
-        for (int64_t j = 0; j < hi - lo; ++j) {
+        for (int64_t j = 0; j < len; ++j) {
             uint32_t d;
             if (canon_delay) {
-                d = canon_delay[lo + j];
+                d = canon_delay[cb + j];
             } else {
                 uint32_t t, sl;
                 gen_synapse(g, p, (uint32_t)j, t, d, sl);
             }
             const int64_t pos = lo + off[d - 1] + used[d];
             used[d]++;
-            const int64_t o = lo - out_base + j;
+            const int64_t o = cb - out_base + j;
             if (o_tgt) o_tgt[o] = (int32_t)target_gid(n, p / n.npc, pos);
             if (o_delay) o_delay[o] = (uint8_t)d;
             if (o_w) o_w[o] = n.w[pos];

@@ -39,8 +39,10 @@ struct DevCounters {
 struct DevNet {
     uint32_t N, npc, ne, C, D;       // neurons, per column, excitatory per column, columns, max delay
     uint32_t D_inh;                  // largest delay of an inhibitory synapse (1 for generated nets)
-    uint32_t uniform_m;              // > 0: row p starts at p * uniform_m (generated nets)
-    int64_t S;                       // synapses
+    uint32_t uniform_m;              // > 0: row p starts at p * uniform_m (generated nets; the
+                                     //       row stride, a multiple of 8 for compact targets)
+    uint32_t canon_m;                // generated nets: synapses per row (the fan-out M)
+    int64_t S;                       // stored synapse slots (rows padded to the stride)
     const int64_t *row_off;          // [N + 1] first synapse of every source row
     const uint16_t *doff;            // [N][kDoffStride]: synapses of delay <= d, d = 0..D
     int32_t *tgt;                    // [S] target gid (explicit nets / big columns), or NULL
@@ -116,6 +118,7 @@ __host__ __device__ __forceinline__ uint32_t draw_below(uint32_t r, uint32_t n)
 // individual delay" and "Bidimensional arrays of neural columns").
 struct GenParams {
     uint32_t npc, ne, m, D, gx, gy;
+    uint32_t m_store;                // row stride (>= m; the tail of a row is padding)
     uint32_t ring_end[4];            // ordinals of ring k are [ring_end[k-1], ring_end[k])
     uint32_t seed_lo, seed_hi;
     int32_t w_exc0, w_inh0;
@@ -206,6 +209,17 @@ __device__ __forceinline__ bool dense_selected(const DevNet &n, int t)
 __device__ __forceinline__ int64_t row_base(const DevNet &n, uint32_t p)
 {
     return n.uniform_m ? (int64_t)p * n.uniform_m : n.row_off[p];
+}
+
+// synapses of row p, and the canonical (unpadded) index of its first synapse
+__device__ __forceinline__ int64_t row_len(const DevNet &n, uint32_t p)
+{
+    return n.uniform_m ? (int64_t)n.canon_m : n.row_off[p + 1] - n.row_off[p];
+}
+
+__device__ __forceinline__ int64_t canon_base(const DevNet &n, uint32_t p)
+{
+    return n.uniform_m ? (int64_t)p * n.canon_m : n.row_off[p];
 }
 
 __device__ __forceinline__ unsigned lanemask_lt()

@@ -271,11 +271,14 @@ __global__ void __launch_bounds__(512) k_dense(DevNet n, const int *t_now)
         s_lutm[i] = n.lut_m[i];
     }
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < kSlots * npc; i += blockDim.x) {
-        const uint32_t sl = i / npc, loc = i - sl * npc;
-        const int lag = t - n.last_spike[s_col[sl] * npc + loc];
-        s_lag[i] = (uint8_t)min(lag, 255);
-        s_in[i] = 0;
+    for (int sl = 0; sl < kSlots; ++sl) {
+        const int32_t *ls = n.last_spike + (size_t)s_col[sl] * npc;
+        uint8_t *lag_row = s_lag + sl * npc;
+        int32_t *in_row = s_in + sl * npc;
+        for (uint32_t loc = threadIdx.x; loc < npc; loc += blockDim.x) {
+            lag_row[loc] = (uint8_t)min(t - ls[loc], 255);
+            in_row[loc] = 0;
+        }
     }
     __syncthreads();
     drive(n, t, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
@@ -320,73 +323,99 @@ __global__ void __launch_bounds__(512) k_dense(DevNet n, const int *t_now)
         __syncwarp();
         if (busy) {
             const int m = off[D];
-            const int64_t base = row_base(n, p);
-            const uint16_t *rt = n.tgt16 + base;
-            int32_t *rw = n.w + base;
-            int32_t *rs = n.sd + base;
-            int d = 1;
-            // kUnroll positions per lane: the target, weight and sd loads of all
-            // of them are issued before any is used
-            for (int k0 = lane; k0 < m; k0 += 32 * kUnroll) {
-                uint32_t v[kUnroll];
-                int32_t sv[kUnroll], wv[kUnroll], am[kUnroll];
-                bool fl[kUnroll], act[kUnroll];
+            const int64_t base = row_base(n, p);     // a multiple of 8: rows are padded
+            const uint4 *rt4 = reinterpret_cast<const uint4 *>(n.tgt16 + base);
+            int4 *rw4 = reinterpret_cast<int4 *>(n.w + base);
+            int4 *rs4 = reinterpret_cast<int4 *>(n.sd + base);
+            const bool all_deriv = exc && deriv_on;
+            // lane takes 8 consecutive synapses per pass: one 16-byte load of
+            // targets, two of weights, two of derivatives
+            for (int c = lane; c * 8 < m; c += 32) {
+                const int k0 = c * 8;
+                int lo = 1, hi = D;                   // bucket of k0: first d with end > k0
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (w_off[mid] > k0) hi = mid; else lo = mid + 1;
+                }
+                int d = lo;
+                uint32_t vmask = 0, fmask = 0;
+                int32_t am[8];
+                bool need_w = all_deriv, need_sd = all_deriv;
 #pragma unroll
-                for (int u = 0; u < kUnroll; ++u) {
-                    const int k = k0 + 32 * u;
-                    fl[u] = false;
+                for (int u = 0; u < 8; ++u) {
                     am[u] = 0;
-                    act[u] = false;
-                    v[u] = 0;
-                    sv[u] = 0;
-                    wv[u] = 0;
+                    const int k = k0 + u;
                     if (k < m) {
                         while (k >= w_off[d]) ++d;
-                        fl[u] = w_flag[d] != 0;
-                        am[u] = w_amt[d];
-                        act[u] = fl[u] || (exc && (am[u] || deriv_on));
-                        if (act[u]) {
-                            v[u] = rt[k];
-                            if (exc) sv[u] = rs[k];
-                            if (fl[u] || (exc && deriv_on)) wv[u] = rw[k];
+                        vmask |= 1u << u;
+                        if (w_flag[d]) {
+                            fmask |= 1u << u;
+                            need_w = true;
+                            need_sd |= exc && stdp;
                         }
+                        if (exc) am[u] = w_amt[d];
+                        need_sd |= am[u] != 0;
                     }
                 }
+                if (!need_w && !need_sd) continue;
+                const uint4 tv = rt4[c];
+                int4 wa = make_int4(0, 0, 0, 0), wb = wa, sa = wa, sb = wa;
+                if (need_w) {
+                    wa = rw4[2 * c];
+                    wb = rw4[2 * c + 1];
+                }
+                if (need_sd) {
+                    sa = rs4[2 * c];
+                    sb = rs4[2 * c + 1];
+                }
+                const uint32_t tw[4] = {tv.x, tv.y, tv.z, tv.w};
+                int32_t wv[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+                int32_t sv[8] = {sa.x, sa.y, sa.z, sa.w, sb.x, sb.y, sb.z, sb.w};
+                bool sd_dirty = false;
 #pragma unroll
-                for (int u = 0; u < kUnroll; ++u) {
-                    if (!act[u]) continue;
-                    const int k = k0 + 32 * u;
-                    const uint32_t idx = (v[u] >> 12) * npc + (v[u] & 0xfffu);
+                for (int u = 0; u < 8; ++u) {
+                    const bool f = (fmask >> u) & 1u;
+                    if (!((vmask >> u) & 1u) || !(f || am[u] || all_deriv)) continue;
+                    const uint32_t v = (u & 1) ? (tw[u >> 1] >> 16) : (tw[u >> 1] & 0xffffu);
+                    const uint32_t idx = (v >> 12) * npc + (v & 0xfffu);
                     if (!exc) {
                         atomicAdd(&s_in[idx], wv[u]);
                         continue;
                     }
                     const int lag = s_lag[idx];
                     const bool pot = am[u] && lag == 1;
-                    const int32_t dep = (fl[u] && stdp) ? s_lutm[lag] : 0;
+                    const int32_t dep = (f && stdp) ? s_lutm[lag] : 0;
                     if (ltp_on && lag == 1) visits++;
                     int32_t sdv = sv[u];
                     if (pot) sdv += am[u];
-                    int32_t w_new = wv[u];
                     if (deriv_on) {
-                        w_new = deriv_w(n, wv[u], sdv);
+                        wv[u] = deriv_w(n, wv[u], sdv);
                         sdv = deriv_sd(n, sdv);
-                        rw[k] = w_new;
                     }
-                    if (fl[u]) atomicAdd(&s_in[idx], w_new);
+                    if (f) atomicAdd(&s_in[idx], wv[u]);
                     sdv -= dep;
-                    if (pot || deriv_on || dep) rs[k] = sdv;
+                    sd_dirty |= pot || deriv_on || dep;
+                    sv[u] = sdv;
+                }
+                if (sd_dirty) {
+                    rs4[2 * c] = make_int4(sv[0], sv[1], sv[2], sv[3]);
+                    rs4[2 * c + 1] = make_int4(sv[4], sv[5], sv[6], sv[7]);
+                }
+                if (all_deriv) {
+                    rw4[2 * c] = make_int4(wv[0], wv[1], wv[2], wv[3]);
+                    rw4[2 * c + 1] = make_int4(wv[4], wv[5], wv[6], wv[7]);
                 }
             }
         }
         __syncwarp();
     }
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < kSlots * npc; i += blockDim.x) {
-        const int32_t v = s_in[i];
-        if (v) {
-            const uint32_t sl = i / npc;
-            red_add(&n.I[s_col[sl] * npc + (i - sl * npc)], v);
+    for (int sl = 0; sl < kSlots; ++sl) {
+        int32_t *dst = n.I + (size_t)s_col[sl] * npc;
+        const int32_t *in_row = s_in + sl * npc;
+        for (uint32_t loc = threadIdx.x; loc < npc; loc += blockDim.x) {
+            const int32_t v = in_row[loc];
+            if (v) red_add(&dst[loc], v);
         }
     }
     if (lane != 0) ev_all = ev_exc = 0;

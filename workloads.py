@@ -45,6 +45,10 @@ WORKLOADS = {
     # 8x8 torus, 1125 synapses per neuron, 40/30/20/10 projection mix
     "grid8_m1125": dict(grid_x=8, grid_y=8, fanout=1125, pct_ring=(40, 30, 20, 10),
                         seed=2, sim_ms=5000),
+    # 16x16 torus (320 k neurons, 360 M synapses), same mix: a smaller case of
+    # the same kernels for profiling (a few GB on the device)
+    "grid16_m1125": dict(grid_x=16, grid_y=16, fanout=1125, pct_ring=(40, 30, 20, 10),
+                         seed=4, sim_ms=1000),
     # 64x64 torus (5.12 M neurons, 5.76 G synapses), same mix
     "grid64_m1125": dict(grid_x=64, grid_y=64, fanout=1125, pct_ring=(40, 30, 20, 10),
                          seed=3, sim_ms=2000),
