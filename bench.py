@@ -47,6 +47,7 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="bound of the oracle sample")
     ap.add_argument("--ref-budget-s", type=float, default=150.0, help="wall bound of the reference arm")
+    ap.add_argument("--no-small", action="store_true", help="skip the 1-column latency line")
     return ap.parse_args()
 
 
@@ -152,6 +153,28 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def kernel_source_digest():
+    """sha256 of the sources the step kernels are compiled from."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("snn_step.cu", "snn_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_1310_8478_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def committed_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary of
+    this workload, or None when there is none or the kernel changed since."""
+    p = os.path.join(ROOT, "profiles", "k_%s_%s_dram.json" % (kernel, workload))
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    if d.get("source_sha256") != kernel_source_digest():
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -251,6 +274,24 @@ def main():
                                                     and KE == K)}
         net.close()
 
+        # the 1-column, M = 100 workload is launch/latency bound: its figure is
+        # microseconds per step with CUDA-graph replays (50 steps per graph)
+        small = None
+        if not args.no_small and rank == 0:
+            scfg = workloads.workload("col1_m100")
+            with eng.Network(scfg, stream=stream, raster_capacity=1 << 22) as sn:
+                sn.run(100)
+                torch.cuda.synchronize()
+                a0 = torch.cuda.Event(enable_timing=True)
+                a1 = torch.cuda.Event(enable_timing=True)
+                a0.record(stream)
+                sn.run(1000)
+                a1.record(stream)
+                torch.cuda.synchronize()
+                small = {"workload": "col1_m100 (1 column, 1250 neurons, M=100)", "steps": 1000,
+                         "us_per_step": round(1000.0 * a0.elapsed_time(a1) / 1000.0, 2),
+                         "graph_steps": sn.get_launch()["graph_steps"]}
+
     d_events = c1["e_all"] - c0["e_all"]
     d_exc = c1["e_exc"] - c0["e_exc"]
     d_ltp = c1["l_exc"] - c0["l_exc"]
@@ -313,11 +354,12 @@ def main():
         "events": d_events, "spikes": d_spikes,
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                     "traffic": None},
+                     "traffic": committed_traffic(dom, args.workload)},
         "kernels": per_kernel,
         "gpu_launches": int(sum(prof[k][0] for k in names)),
         "build_s": round(t_build, 2),
         "e2e": e2e,
+        "small_net": small,
         "cpu_baseline": None if cpu is None else {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")},
         "clocks": clk,
     }
