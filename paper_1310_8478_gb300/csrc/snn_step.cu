@@ -78,16 +78,19 @@ __device__ __forceinline__ void drive(const DevNet &n, int t, uint32_t gtid, uin
 // ---------------------------------------------------------------------------
 // sparse S1: work items are (spike, delay) pairs -- every excitatory spike of
 // step t - d for d = 1..D and every inhibitory spike of step t - d for
-// d = 1..D_inh (generated nets: inhibitory synapses all have delay 1).  One
-// warp walks an item's delay bucket with coalesced loads; lanes add the
-// weight into the target's Q16 input with a fire-and-forget L2 reduction and,
-// on plastic synapses, subtract the LTD amount at lag t - last_spike[target].
+// d = 1..D_inh (generated nets: inhibitory synapses all have delay 1).  Lanes
+// add the weight into the target's Q16 input with a fire-and-forget L2
+// reduction and, on plastic synapses, subtract the LTD amount at lag
+// t - last_spike[target].
 // ---------------------------------------------------------------------------
-__global__ void k_deliver(DevNet n, const int *t_now)
+__global__ void __launch_bounds__(1024) k_deliver(DevNet n, const int *t_now)
 {
     __shared__ int32_t s_lut[kLut];
     __shared__ int s_start[2 * 32 + 1];
     __shared__ const int32_t *s_list[2 * 32];
+    __shared__ int64_t s_tile_lo[32 * 32];       // per warp: first synapse of each of its 32 items
+    __shared__ int s_tile_start[32 * 33];        // per warp: prefix of the items' lengths
+    __shared__ uint32_t s_tile_info[32 * 32];    // per warp: kind and source column of each item
     const int t = *t_now;
     if (dense_selected(n, t)) return;
     const bool stdp = !(n.flags & SNN_STDP_OFF);
@@ -117,35 +120,68 @@ __global__ void k_deliver(DevNet n, const int *t_now)
     drive(n, t, gtid, gthreads);
 
     const int total = s_start[nl];
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t warps = gthreads >> 5;
     unsigned long long ev_all = 0, ev_exc = 0;
-    for (uint32_t item = gtid >> 5; item < (uint32_t)total; item += warps) {
-        int l = 0;
-        while (s_start[l + 1] <= (int)item) ++l;
-        const int idx = (int)item - s_start[l];
-        const bool inh = l >= (int)n.D;
-        const int d = inh ? l - (int)n.D + 1 : l + 1;
-        const uint32_t p = (uint32_t)(inh ? s_list[l][n.N - 1 - idx] : s_list[l][idx]);
-        const uint32_t col = p / n.npc;
-        const uint16_t *off = n.doff + (size_t)p * kDoffStride;
-        const int64_t base = row_base(n, p);
-        const int64_t lo = base + off[d - 1], hi = base + off[d];
-        ev_all += (unsigned long long)(hi - lo);
-        if (!inh) ev_exc += (unsigned long long)(hi - lo);
-        if (!inh && stdp) {
-            for (int64_t k = lo + lane; k < hi; k += 32) {
-                const uint32_t tg = target_gid(n, col, k);
-                red_add(&n.I[tg], n.w[k]);
+    // A warp takes 32 items at a time (one per lane), prefix-sums their bucket
+    // lengths and walks the concatenated synapses with all 32 lanes, so short
+    // buckets do not leave lanes idle.
+    int64_t *w_lo = s_tile_lo + warp * 32;
+    int *w_start = s_tile_start + warp * 33;
+    uint32_t *w_info = s_tile_info + warp * 32;
+    for (uint32_t tile = (gtid >> 5) * 32; tile < (uint32_t)total; tile += warps * 32) {
+        const uint32_t item = tile + lane;
+        int len = 0;
+        int64_t lo = 0;
+        uint32_t info = 0;                       // bit 0: excitatory; bits 1..: source column
+        if (item < (uint32_t)total) {
+            int l = 0;
+            while (s_start[l + 1] <= (int)item) ++l;
+            const int idx = (int)item - s_start[l];
+            const bool inh = l >= (int)n.D;
+            const int d = inh ? l - (int)n.D + 1 : l + 1;
+            const uint32_t p = (uint32_t)(inh ? s_list[l][n.N - 1 - idx] : s_list[l][idx]);
+            const uint16_t *off = n.doff + (size_t)p * kDoffStride;
+            lo = row_base(n, p) + off[d - 1];
+            len = (int)off[d] - (int)off[d - 1];
+            info = (inh ? 0u : 1u) | ((p / n.npc) << 1);
+        }
+        int incl = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int tile_len = __shfl_sync(0xffffffffu, incl, 31);
+        const int exc_len = __reduce_add_sync(0xffffffffu, (info & 1u) ? len : 0);
+        w_lo[lane] = lo;
+        w_start[lane] = incl - len;
+        w_info[lane] = info;
+        if (lane == 0) {
+            w_start[32] = tile_len;
+            ev_all += (unsigned long long)tile_len;
+            ev_exc += (unsigned long long)exc_len;
+        }
+        __syncwarp();
+        int j = 0;
+        for (int e = lane; e < tile_len; e += 32) {
+            while (w_start[j + 1] <= e) ++j;
+            const int64_t k = w_lo[j] + (e - w_start[j]);
+            const uint32_t inf = w_info[j];
+            const bool exc = inf & 1u;
+            const int32_t wk = n.w[k];
+            const int32_t sk = (exc && stdp) ? n.sd[k] : 0;
+            const uint32_t tg = target_gid(n, inf >> 1, k);
+            red_add(&n.I[tg], wk);
+            if (exc && stdp) {
                 const int lag = t - n.last_spike[tg];          // >= 1
                 if (lag < kLut) {
                     const int32_t a = s_lut[lag];
-                    if (a) n.sd[k] -= a;
+                    if (a) n.sd[k] = sk - a;
                 }
             }
-        } else {
-            for (int64_t k = lo + lane; k < hi; k += 32) red_add(&n.I[target_gid(n, col, k)], n.w[k]);
         }
+        __syncwarp();
     }
     if (lane != 0) ev_all = ev_exc = 0;
     const unsigned long long ba = block_sum(ev_all);
@@ -181,16 +217,34 @@ __global__ void k_ltp(DevNet n, const int *t_now, int force)
          item += warps) {
         const int32_t post = (int)item < ce ? ring[item] : ring[n.N - 1 - ((int)item - ce)];
         const int64_t lo = n.rin_off[post], hi = n.rin_off[post + 1];
-        for (int64_t e = lo + lane; e < hi; e += 32) {
-            const uint64_t r = n.rin[e];
-            const uint32_t pre = (uint32_t)r;
-            const uint32_t ord = (uint32_t)(r >> 32) & 0xffffu;
-            const uint32_t d = (uint32_t)(r >> 48);
-            const uint32_t recent = n.hist[pre] & (0xffffffffu << d);
-            const int lag = recent ? (__ffs(recent) - 1 - (int)d) : (tp - n.last_old[pre] - (int)d);
-            if (lag < kLut) {
-                const int32_t a = s_lut[lag];
-                if (a) n.sd[row_base(n, pre) + ord] += a;
+        // kUnroll entries per lane: reverse entries, then the sources'
+        // histories and the synapses' derivatives (independent) in one round
+        for (int64_t e0 = lo + lane; e0 < hi; e0 += 32 * kUnroll) {
+            uint64_t r[kUnroll];
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) r[u] = (e0 + 32 * u < hi) ? n.rin[e0 + 32 * u] : ~0ull;
+            uint32_t h[kUnroll];
+            int32_t sv[kUnroll];
+            int64_t pos[kUnroll];
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+                if (r[u] == ~0ull) continue;
+                const uint32_t pre = (uint32_t)r[u];
+                pos[u] = row_base(n, pre) + ((uint32_t)(r[u] >> 32) & 0xffffu);
+                h[u] = n.hist[pre];
+                sv[u] = n.sd[pos[u]];
+            }
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+                if (r[u] == ~0ull) continue;
+                const uint32_t pre = (uint32_t)r[u];
+                const uint32_t d = (uint32_t)(r[u] >> 48);
+                const uint32_t recent = h[u] & (0xffffffffu << d);
+                const int lag = recent ? (__ffs(recent) - 1 - (int)d) : (tp - n.last_old[pre] - (int)d);
+                if (lag < kLut) {
+                    const int32_t a = s_lut[lag];
+                    if (a) n.sd[pos[u]] = sv[u] + a;
+                }
             }
         }
     }
@@ -483,26 +537,44 @@ __global__ void k_neuron(DevNet n, const int *t_now, int *t_next)
     const uint32_t first = blockIdx.x * tile;
     uint32_t fe = 0, fi = 0;          // bit it: neuron first + it * blockDim + tid fired
     unsigned long long indeg = 0;     // excitatory in-degree of the neurons that fired
+    // all loads of the thread's neurons first, then the updates and stores
+    int32_t iq[kNeuronsPerThread];
+    float vv[kNeuronsPerThread], uu[kNeuronsPerThread];
+    uint32_t hh[kNeuronsPerThread];
+#pragma unroll
+    for (int it = 0; it < kNeuronsPerThread; ++it) {
+        const uint32_t i = first + it * blockDim.x + threadIdx.x;
+        if (i < n.N) {
+            iq[it] = n.I[i];
+            vv[it] = n.v[i];
+            uu[it] = n.u[i];
+            hh[it] = n.hist[i];
+        }
+    }
 #pragma unroll
     for (int it = 0; it < kNeuronsPerThread; ++it) {
         const uint32_t i = first + it * blockDim.x + threadIdx.x;
         if (i >= n.N) break;
         const bool exc = (i % n.npc) < n.ne;
-        const int32_t iq = n.I[i];
+        float v = vv[it], u = uu[it];
+        const bool fired = izhikevich_step(v, u, iq[it], exc);
         n.I[i] = 0;
-        float v = n.v[i], u = n.u[i];
-        const bool fired = izhikevich_step(v, u, iq, exc);
         n.v[i] = v;
         n.u[i] = u;
-        uint32_t h = n.hist[i];
+        uint32_t h = hh[it];
         if (h & 0x80000000u) n.last_old[i] = t - 32;
         h = (h << 1) | (fired ? 1u : 0u);
         n.hist[i] = h;
         if (fired) {
             n.last_spike[i] = t;
-            indeg += (unsigned long long)(n.rin_off[i + 1] - n.rin_off[i]);
             if (exc) fe |= 1u << it; else fi |= 1u << it;
         }
+    }
+#pragma unroll
+    for (int it = 0; it < kNeuronsPerThread; ++it) {
+        if (!(((fe | fi) >> it) & 1u)) continue;
+        const uint32_t i = first + it * blockDim.x + threadIdx.x;
+        indeg += (unsigned long long)(n.rin_off[i + 1] - n.rin_off[i]);
     }
     // block-wide exclusive prefix of the per-thread counts (exc, inh)
     __shared__ int s_w[2][32];

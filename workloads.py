@@ -54,6 +54,16 @@ WORKLOADS = {
                          seed=3, sim_ms=2000),
 }
 
+# The paper's own geometry (Sec. 2 and Table 1): columns of 1000 neurons (800
+# RS, 200 FS), M = 200 synapses per neuron, 76/12/8/4 projection mix; grid
+# sizes of Table 1 (200 K ... 6.6 G synapses).  Neuron, STDP and plasticity
+# constants as above (the paper does not print its weights).
+PAPER_GRIDS = {"1x1": (1, 1), "2x2": (2, 2), "4x4": (4, 4), "8x8": (8, 8), "16x16": (16, 16),
+               "32x32": (32, 32), "64x64": (64, 64), "128x128": (128, 128), "256x128": (256, 128)}
+for _name, (_gx, _gy) in PAPER_GRIDS.items():
+    WORKLOADS["paper_" + _name] = dict(grid_x=_gx, grid_y=_gy, neurons_per_col=1000, exc_per_col=800,
+                                       fanout=200, pct_ring=(76, 12, 8, 4), seed=7, sim_ms=2000)
+
 
 def workload(name: str, **overrides) -> dict:
     """Full parameter dictionary of a named workload (a fresh copy)."""
