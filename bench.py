@@ -51,6 +51,19 @@ def parse_args():
     return ap.parse_args()
 
 
+def combine_ranks(ms: float, events: float, dist=None, device="cpu"):
+    """Whole-job figures of a replicas run: the slowest rank's time and the
+    sum of every rank's synaptic events."""
+    if dist is None:
+        return ms, events
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e = torch.tensor([float(events)], dtype=torch.float64, device=device)
+    dist.all_reduce(e)
+    return float(t.item()), float(e.item())
+
+
 def dist_env():
     return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
             int(os.environ.get("WORLD_SIZE", "1")))
@@ -296,15 +309,7 @@ def main():
     d_exc = c1["e_exc"] - c0["e_exc"]
     d_ltp = c1["l_exc"] - c0["l_exc"]
     d_spikes = c1["spikes"] - c0["spikes"]
-    if dist is not None:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        ev = torch.tensor([d_events], dtype=torch.float64, device="cuda")
-        dist.all_reduce(ev)
-        total_events = float(ev.item())
-    else:
-        total_events = float(d_events)
+    ms, total_events = combine_ranks(ms, d_events, dist, "cuda")
     if rank != 0:
         return 0
 

@@ -258,8 +258,8 @@ size_t footprint(const snn_config *c, uint32_t N, int64_t S, int64_t n_rin, bool
     b += (size_t)c->grid_x * c->grid_y * kSlotStride * 4;                                  // neighbour table
     b += (size_t)N * kDoffStride * 2;             // delay offsets
     b += ((size_t)N + 1) * 8 * 2;                 // row_off, rin_off
-    b += (size_t)n_rin * 8;                       // reverse index
-    b += (size_t)N * 24;                          // v u I hist last_old last_spike
+    b += (size_t)n_rin * 12;                      // reverse index + its LTP accumulator
+    b += (size_t)N * 24;                          // v u I (hist, last_old) last_spike
     b += D * N * 4 + D * 8;                       // ring
     b += (size_t)N * 12 + ((size_t)N / 1024 + 2) * 8;  // build scratch
     if (explicit_net) b += (size_t)S;             // canonical delays
@@ -300,8 +300,7 @@ int alloc_common(snn_net *net)
     SNN_TRY(dalloc_t(net, (size_t)N, &dn.v));
     SNN_TRY(dalloc_t(net, (size_t)N, &dn.u));
     SNN_TRY(dalloc_t(net, (size_t)N, &dn.I));
-    SNN_TRY(dalloc_t(net, (size_t)N, &dn.hist));
-    SNN_TRY(dalloc_t(net, (size_t)N, &dn.last_old));
+    SNN_TRY(dalloc_t(net, (size_t)N, &dn.hl));
     SNN_TRY(dalloc_t(net, (size_t)N, &dn.last_spike));
     SNN_TRY(dalloc_t(net, (size_t)D * N, &dn.ring_ids));
     SNN_TRY(dalloc_t(net, (size_t)2 * D, &dn.ring_cnt));
@@ -426,6 +425,9 @@ int finish_build(snn_net *net)
     net->n_rin = n_rin;
     SNN_TRY(dalloc_t(net, (size_t)std::max<int64_t>(n_rin, 1), &net->rin));
     dn.rin = net->rin;
+    SNN_TRY(dalloc_t(net, (size_t)std::max<int64_t>(n_rin, 1), &dn.sd_rev));
+    SNN_CUDA(cudaMemsetAsync(dn.sd_rev, 0, (size_t)std::max<int64_t>(n_rin, 1) * 4, s));
+    dn.n_rin = n_rin;
     k_fill_reverse<<<g, 256, 0, s>>>(dn, cursor, net->rin);
     SNN_CUDA(cudaGetLastError());
     SNN_CUDA(cudaStreamSynchronize(s));
@@ -539,6 +541,7 @@ void launch_flush(snn_net *net)
     const int32_t t = net->t;
     const int *t_now = &net->ctr->t_slot[t & 1];
     k_ltp<<<grid_for(net, net->launch.ltp_blocks_per_sm), net->launch.ltp_block, 0, s>>>(dn, t_now, 1);
+    k_fold<<<grid_for(net, 8), 256, 0, s>>>(dn);
     const uint32_t P = net->cfg.deriv_period_ms;
     if (P && t > 0 && (uint32_t)t % P == 0)
         k_deriv<<<dim3(deriv_grid_x(net), dn.C), net->launch.deriv_block, 0, s>>>(dn, t_now, 1);
@@ -564,7 +567,10 @@ void launch_step(snn_net *net, int32_t t)
     k_ltp<<<grid_for(net, L.ltp_blocks_per_sm), L.ltp_block, 0, s>>>(dn, t_now, 0);
     mark(2);
     if (P && t > 0 && (uint32_t)t % P == 0) {
+        // the long-term update needs the whole derivative: fold the
+        // event-driven LTP first (both passes read sd afterwards)
         mark(3);
+        k_fold<<<grid_for(net, 8), 256, 0, s>>>(dn);
         k_deriv<<<dim3(deriv_grid_x(net), dn.C), L.deriv_block, 0, s>>>(dn, t_now, 0);
         mark(3);
     }
@@ -1102,6 +1108,7 @@ int snn_reset(snn_net *net)
     cudaStream_t s = net->stream;
     const int g = grid_for(net, 8);
     k_reset_weights<<<g, 256, 0, s>>>(net->dn, net->gen.w_exc0, net->gen.w_inh0);
+    SNN_CUDA(cudaMemsetAsync(net->dn.sd_rev, 0, (size_t)std::max<int64_t>(net->n_rin, 1) * 4, s));
     k_init_state<<<g, 256, 0, s>>>(net->dn);
     DevCounters hc{};
     hc.raster_first_drop_t = 0x7fffffff;
@@ -1365,9 +1372,9 @@ int snn_save_state(snn_net *net, void *host_buf, size_t cap, size_t *n)
     p += sizeof h;
     cudaStream_t s = net->stream;
     const DevNet &dn = net->dn;
-    const void *src[] = {dn.v, dn.u, dn.I, dn.hist, dn.last_old, dn.last_spike, dn.ring_ids, dn.ring_cnt, net->w, net->sd, net->ctr};
-    const size_t len[] = {N * 4, N * 4, N * 4, N * 4, N * 4, N * 4, D * N * 4, D * 8, S * 4, S * 4, sizeof(DevCounters)};
-    for (int k = 0; k < 11; ++k) {
+    const void *src[] = {dn.v, dn.u, dn.I, dn.hl, dn.last_spike, dn.ring_ids, dn.ring_cnt, net->w, net->sd, net->ctr};
+    const size_t len[] = {N * 4, N * 4, N * 4, N * 8, N * 4, D * N * 4, D * 8, S * 4, S * 4, sizeof(DevCounters)};
+    for (int k = 0; k < 10; ++k) {
         if (len[k]) SNN_CUDA(cudaMemcpyAsync(p, src[k], len[k], cudaMemcpyDeviceToHost, s));
         p += len[k];
     }
@@ -1391,13 +1398,14 @@ int snn_load_state(snn_net *net, const void *host_buf, size_t n)
     const char *p = (const char *)host_buf + sizeof h;
     cudaStream_t s = net->stream;
     DevNet &dn = net->dn;
-    void *dst[] = {dn.v, dn.u, dn.I, dn.hist, dn.last_old, dn.last_spike, dn.ring_ids, dn.ring_cnt, net->w, net->sd, net->ctr};
-    const size_t len[] = {N * 4, N * 4, N * 4, N * 4, N * 4, N * 4, D * N * 4, D * 8, S * 4, S * 4, sizeof(DevCounters)};
-    for (int k = 0; k < 11; ++k) {
+    void *dst[] = {dn.v, dn.u, dn.I, dn.hl, dn.last_spike, dn.ring_ids, dn.ring_cnt, net->w, net->sd, net->ctr};
+    const size_t len[] = {N * 4, N * 4, N * 4, N * 8, N * 4, D * N * 4, D * 8, S * 4, S * 4, sizeof(DevCounters)};
+    for (int k = 0; k < 10; ++k) {
         if (len[k]) SNN_CUDA(cudaMemcpyAsync(dst[k], p, len[k], cudaMemcpyHostToDevice, s));
         p += len[k];
     }
     SNN_CUDA(cudaStreamSynchronize(s));
+    SNN_CUDA(cudaMemsetAsync(dn.sd_rev, 0, (size_t)std::max<int64_t>(net->n_rin, 1) * 4, s));
     net->t = h.t;
     net->ltp_owed = false;
     // the raster restarts at the checkpoint's step

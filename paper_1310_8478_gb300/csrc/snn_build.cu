@@ -232,8 +232,7 @@ __global__ void k_init_state(DevNet n)
         n.v[i] = v0;
         n.u[i] = __fmul_rn(0.2f, v0);
         n.I[i] = 0;
-        n.hist[i] = 0u;
-        n.last_old[i] = kNever;
+        n.hl[i] = make_uint2(0u, (uint32_t)kNever);
         n.last_spike[i] = kNever;
     }
 }

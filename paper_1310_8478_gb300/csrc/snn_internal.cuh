@@ -51,10 +51,16 @@ struct DevNet {
     int32_t *w, *sd;                 // [S] weight, STDP derivative; rows sorted by delay
     const int64_t *rin_off;          // [N + 1] reverse index (incoming excitatory synapses)
     const uint64_t *rin;             // source | ordinal-in-row << 32 | delay << 48
+    int32_t *sd_rev;                 // [n_rin] LTP of the event-driven pass, accumulated in
+                                     //         reverse-index order (contiguous per target);
+                                     //         folded into sd before every long-term update
+                                     //         and every read
+    int64_t n_rin;
     float *v, *u;                    // [N] membrane potential, recovery variable
     int32_t *I;                      // [N] Q16 input accumulated during S1/S2
-    uint32_t *hist;                  // [N] bit k: fired at step t - k
-    int32_t *last_old;               // [N] latest spike older than the 32-step window
+    uint2 *hl;                       // [N] x: bit k = fired at step t - k; y: latest spike
+                                     //     older than that 32-step window (one 8-byte word,
+                                     //     so the LTP gather is a single access)
     int32_t *last_spike;             // [N] latest spike
     int32_t *ring_ids;               // [D][N] spike ids of step s in slot s % D: exc from the
                                      //         front, inh from the back
@@ -249,6 +255,7 @@ __global__ void k_dense(DevNet n, const int *t_now);
 __global__ void k_neuron(DevNet n, const int *t_now, int *t_next);
 __global__ void k_ltp(DevNet n, const int *t_now, int force);
 __global__ void k_deriv(DevNet n, const int *t_now, int force);
+__global__ void k_fold(DevNet n);
 
 size_t dense_smem_bytes(uint32_t npc, uint32_t block);
 

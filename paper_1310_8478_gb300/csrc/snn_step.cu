@@ -12,8 +12,11 @@
 // i.e. the potentiation owed by the previous step travels with this step's
 // delivery, so that one pass over the synapses can do both.  Two
 // interchangeable implementations of the first bracket exist:
-//   sparse (event driven): k_ltp (reverse index of the spikers of t-1),
-//       k_deriv, k_deliver ((spike, delay) items over the delay buckets);
+//   sparse (event driven): k_ltp (reverse index of the spikers of t-1; the
+//       amounts accumulate in sd_rev, laid out like the reverse index so the
+//       updates of one target are contiguous), k_fold (sd += sd_rev before a
+//       long-term update), k_deriv, k_deliver ((spike, delay) items over the
+//       delay buckets);
 //   dense: k_dense streams every source row once, in per-synapse order
 //       LTP(t-1) -> long-term update -> delivery + LTD(t), with the target
 //       columns' input and post-spike lags staged in shared memory.
@@ -198,7 +201,7 @@ __global__ void __launch_bounds__(1024) k_deliver(DevNet n, const int *t_now)
 // t - 1 is the lowest set bit k >= d of the source's 32-step history (lag
 // k - d), else its latest older spike last_old (lag t - 1 - last_old - d).
 // ---------------------------------------------------------------------------
-__global__ void k_ltp(DevNet n, const int *t_now, int force)
+__global__ void __launch_bounds__(1024) k_ltp(DevNet n, const int *t_now, int force)
 {
     __shared__ int32_t s_lut[kLut];
     const int t = *t_now;
@@ -223,30 +226,42 @@ __global__ void k_ltp(DevNet n, const int *t_now, int force)
             uint64_t r[kUnroll];
 #pragma unroll
             for (int u = 0; u < kUnroll; ++u) r[u] = (e0 + 32 * u < hi) ? n.rin[e0 + 32 * u] : ~0ull;
-            uint32_t h[kUnroll];
+            uint2 h[kUnroll];
             int32_t sv[kUnroll];
-            int64_t pos[kUnroll];
 #pragma unroll
             for (int u = 0; u < kUnroll; ++u) {
                 if (r[u] == ~0ull) continue;
-                const uint32_t pre = (uint32_t)r[u];
-                pos[u] = row_base(n, pre) + ((uint32_t)(r[u] >> 32) & 0xffffu);
-                h[u] = n.hist[pre];
-                sv[u] = n.sd[pos[u]];
+                h[u] = n.hl[(uint32_t)r[u]];
+                sv[u] = n.sd_rev[e0 + 32 * u];
             }
 #pragma unroll
             for (int u = 0; u < kUnroll; ++u) {
                 if (r[u] == ~0ull) continue;
-                const uint32_t pre = (uint32_t)r[u];
                 const uint32_t d = (uint32_t)(r[u] >> 48);
-                const uint32_t recent = h[u] & (0xffffffffu << d);
-                const int lag = recent ? (__ffs(recent) - 1 - (int)d) : (tp - n.last_old[pre] - (int)d);
+                const uint32_t recent = h[u].x & (0xffffffffu << d);
+                const int lag = recent ? (__ffs(recent) - 1 - (int)d) : (tp - (int)h[u].y - (int)d);
                 if (lag < kLut) {
                     const int32_t a = s_lut[lag];
-                    if (a) n.sd[pos[u]] = sv[u] + a;
+                    if (a) n.sd_rev[e0 + 32 * u] = sv[u] + a;   // coalesced: the target's entries are contiguous
                 }
             }
         }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// fold the event-driven LTP accumulated in reverse order into the forward
+// derivatives (each forward excitatory synapse has exactly one reverse entry)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_fold(DevNet n)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n.n_rin; e += stride) {
+        const int32_t v = n.sd_rev[e];
+        if (!v) continue;
+        const uint64_t r = n.rin[e];
+        n.sd[row_base(n, (uint32_t)r) + ((uint32_t)(r >> 32) & 0xffffu)] += v;
+        n.sd_rev[e] = 0;
     }
 }
 
@@ -255,7 +270,7 @@ __global__ void k_ltp(DevNet n, const int *t_now, int force)
 // excitatory rows of column blockIdx.y (rows c*npc .. c*npc+ne-1 are
 // contiguous): w = clamp(w + bias + sd, 0, wmax), sd = (sd*decay + 2^15) >> 16.
 // ---------------------------------------------------------------------------
-__global__ void k_deriv(DevNet n, const int *t_now, int force)
+__global__ void __launch_bounds__(1024) k_deriv(DevNet n, const int *t_now, int force)
 {
     const int t = *t_now;
     if (n.ctr->ltp_pending != t - 1) return;
@@ -346,7 +361,8 @@ __global__ void __launch_bounds__(512) k_dense(DevNet n, const int *t_now)
     for (uint32_t r = r0 + warp; r < r1; r += nwarps) {
         const uint32_t p = col * npc + r;
         const bool exc = r < n.ne;
-        const uint32_t h = n.hist[p];                 // bit k: fired at t - 1 - k
+        const uint2 hv = n.hl[p];
+        const uint32_t h = hv.x;                      // bit k: fired at t - 1 - k
         const uint16_t *off = n.doff + (size_t)p * kDoffStride;
         // lane d (1..D) prepares bucket d
         int len = 0;
@@ -359,7 +375,7 @@ __global__ void __launch_bounds__(512) k_dense(DevNet n, const int *t_now)
             fl = (deliver_on && ((h >> (lane - 1)) & 1u)) ? 1u : 0u;
             if (exc && ltp_on && len) {
                 const uint32_t recent = h & (0xffffffffu << lane);
-                const int lag = recent ? (__ffs(recent) - 1 - lane) : (t - 1 - n.last_old[p] - lane);
+                const int lag = recent ? (__ffs(recent) - 1 - lane) : (t - 1 - (int)hv.y - lane);
                 amt = lag < kLut ? s_lutp[lag] : 0;
             }
             w_flag[lane] = fl;
@@ -529,7 +545,7 @@ __device__ __forceinline__ bool izhikevich_step(float &v, float &u, int32_t iq, 
     return false;
 }
 
-__global__ void k_neuron(DevNet n, const int *t_now, int *t_next)
+__global__ void __launch_bounds__(1024) k_neuron(DevNet n, const int *t_now, int *t_next)
 {
     const int t = *t_now;
     const int par = t & 1;
@@ -540,7 +556,7 @@ __global__ void k_neuron(DevNet n, const int *t_now, int *t_next)
     // all loads of the thread's neurons first, then the updates and stores
     int32_t iq[kNeuronsPerThread];
     float vv[kNeuronsPerThread], uu[kNeuronsPerThread];
-    uint32_t hh[kNeuronsPerThread];
+    uint2 hh[kNeuronsPerThread];
 #pragma unroll
     for (int it = 0; it < kNeuronsPerThread; ++it) {
         const uint32_t i = first + it * blockDim.x + threadIdx.x;
@@ -548,7 +564,7 @@ __global__ void k_neuron(DevNet n, const int *t_now, int *t_next)
             iq[it] = n.I[i];
             vv[it] = n.v[i];
             uu[it] = n.u[i];
-            hh[it] = n.hist[i];
+            hh[it] = n.hl[i];
         }
     }
 #pragma unroll
@@ -561,10 +577,10 @@ __global__ void k_neuron(DevNet n, const int *t_now, int *t_next)
         n.I[i] = 0;
         n.v[i] = v;
         n.u[i] = u;
-        uint32_t h = hh[it];
-        if (h & 0x80000000u) n.last_old[i] = t - 32;
-        h = (h << 1) | (fired ? 1u : 0u);
-        n.hist[i] = h;
+        uint2 h = hh[it];
+        if (h.x & 0x80000000u) h.y = (uint32_t)(t - 32);
+        h.x = (h.x << 1) | (fired ? 1u : 0u);
+        n.hl[i] = h;
         if (fired) {
             n.last_spike[i] = t;
             if (exc) fe |= 1u << it; else fi |= 1u << it;
