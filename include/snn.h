@@ -286,6 +286,40 @@ int snn_save_state(snn_net *net, void *host_buf, size_t cap, size_t *n);
 int snn_load_state(snn_net *net, const void *host_buf, size_t n);
 
 /*
+ * snn_autotune -- pick the fastest launch shape for this net: every candidate
+ * shape (rows per dense block, resident blocks of the event-driven kernels,
+ * neuron block, steps per graph) runs probe_ms steps from a reset, timed with
+ * CUDA events; the best is kept and the net is left reset at t = 0.  Results
+ * never depend on the shape.  Generated nets only (SNN_ESTATE otherwise).
+ * *best (may be NULL) receives the chosen shape.
+ */
+int snn_autotune(snn_net *net, uint32_t probe_ms, snn_launch *best);
+
+/*
+ * Batches: many independent networks on one GPU (the paper's networks of
+ * different sizes and fan-outs, Table 3, run side by side).  A batch advances
+ * every net it holds with one CUDA-graph launch per chunk of graph_steps
+ * steps; each net's kernels form a parallel branch of the graph, so small,
+ * launch-bound nets run concurrently instead of one after another.  Each net
+ * keeps its own state, stream-independent and bit-identical to running it
+ * alone.  The batch owns no net: free the batch before its nets.  All nets
+ * must be on the current device, share deriv_period_ms, have profiling off
+ * and stand at the same step t.
+ *   graph_steps: steps per captured chunk (even; 0 = 10).
+ * Errors: SNN_EINVAL (empty list, mismatched period), SNN_ESTATE (different
+ * t), SNN_ECUDA.
+ */
+typedef struct snn_batch snn_batch;
+int snn_batch_create(snn_net *const *nets, uint32_t n_nets, uint32_t graph_steps, snn_batch **out);
+
+/* snn_batch_run -- advance every net of the batch n_ms steps; returns after
+   completion and each net's error-word check. */
+int snn_batch_run(snn_batch *batch, uint32_t n_ms);
+
+/* snn_batch_free -- release the batch (not its nets; NULL is allowed). */
+void snn_batch_free(snn_batch *batch);
+
+/*
  * snn_reset -- return a generated net to its initial state (t = 0, initial
  * weights, sd = 0, v = -65 mV, u = 0.2 v, empty ring and raster, counters 0)
  * without rebuilding it; external stimulus is cleared.  SNN_ESTATE for nets

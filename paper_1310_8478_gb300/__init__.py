@@ -2,7 +2,7 @@
 (Paolucci et al., arXiv 1310.8478): CUDA kernels for sm_103a behind the C ABI
 of include/snn.h, with a ctypes binding."""
 from .snn import (  # noqa: F401
-    Network, SnnError, load, library_path, make_config,
+    Network, Batch, SnnError, load, library_path, make_config,
     snn_build_network, snn_build_network_explicit, snn_step, snn_run, snn_free,
     snn_read_raster, snn_read_weights, STDP_OFF, DELIVERY_OFF,
 )

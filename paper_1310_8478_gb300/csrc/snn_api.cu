@@ -109,6 +109,7 @@ struct snn_net {
     int32_t *nbr = nullptr;
     bool ltp_owed = false;          // the last step's LTP has not been applied yet
     bool dense_ok = false;          // the dense pass can run on this net
+    uint64_t version = 0;           // bumped whenever captured launches go stale
     // stimulus
     size_t stim_cap = 0;
     int64_t stim_off_cap = 0;
@@ -124,6 +125,17 @@ struct snn_net {
     size_t ev_used = 0;
     double prof_ms[kKinds] = {0};
     int64_t prof_n[kKinds] = {0};
+};
+
+struct snn_batch {
+    std::vector<snn_net *> nets;
+    cudaStream_t main = nullptr;
+    std::vector<cudaStream_t> branch;
+    cudaEvent_t fork = nullptr;
+    std::vector<cudaEvent_t> join;
+    uint32_t L = 0;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    std::vector<uint64_t> versions[2];   // the nets' versions when each graph was captured
 };
 
 namespace {
@@ -181,6 +193,8 @@ int dalloc_t(snn_net *net, size_t count, T **out)
     return r;
 }
 
+// every change of what the kernels see (DevNet, launch shape) goes through
+// here: captured graphs of the net, and of batches holding it, are stale
 void drop_graphs(snn_net *net)
 {
     for (int i = 0; i < 2; ++i) {
@@ -188,6 +202,7 @@ void drop_graphs(snn_net *net)
         net->graph[i] = nullptr;
     }
     net->graphs_dirty = true;
+    net->version++;
 }
 
 int check_config(const snn_config *c)
@@ -247,6 +262,14 @@ int build_luts(const snn_config *c, std::vector<int32_t> &lut)
 int grid_for(const snn_net *net, uint32_t per_sm)
 {
     return std::max(1, net->sm_count) * (int)std::max(1u, per_sm);
+}
+
+// grid of a grid-stride kernel over `units` work units, `per_block` units per
+// block at most once, capped at blocks_per_sm resident waves
+int sized_grid(const snn_net *net, uint32_t blocks_per_sm, int64_t units, int64_t per_block)
+{
+    const int64_t want = (units + per_block - 1) / per_block;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)grid_for(net, blocks_per_sm)));
 }
 
 // footprint of everything but the raster (bytes)
@@ -541,7 +564,7 @@ void launch_flush(snn_net *net)
     const int32_t t = net->t;
     const int *t_now = &net->ctr->t_slot[t & 1];
     k_ltp<<<grid_for(net, net->launch.ltp_blocks_per_sm), net->launch.ltp_block, 0, s>>>(dn, t_now, 1);
-    k_fold<<<grid_for(net, 8), 256, 0, s>>>(dn);
+    k_fold<<<sized_grid(net, 8, net->n_rin, 4096), 256, 0, s>>>(dn);
     const uint32_t P = net->cfg.deriv_period_ms;
     if (P && t > 0 && (uint32_t)t % P == 0)
         k_deriv<<<dim3(deriv_grid_x(net), dn.C), net->launch.deriv_block, 0, s>>>(dn, t_now, 1);
@@ -549,10 +572,9 @@ void launch_flush(snn_net *net)
     cudaMemcpyAsync(&net->ctr->ltp_pending, &none, sizeof none, cudaMemcpyHostToDevice, s);
 }
 
-void launch_step(snn_net *net, int32_t t)
+void launch_step(snn_net *net, int32_t t, cudaStream_t s)
 {
     const DevNet &dn = net->dn;
-    cudaStream_t s = net->stream;
     const int *t_now = &net->ctr->t_slot[t & 1];
     int *t_next = &net->ctr->t_slot[(t & 1) ^ 1];
     const snn_launch &L = net->launch;
@@ -564,18 +586,21 @@ void launch_step(snn_net *net, int32_t t)
     // [S4(t-1) S5(t-1) S1(t)]: event-driven kernels and the dense pass; the
     // device picks one of the two (the other returns at once)
     mark(2);
-    k_ltp<<<grid_for(net, L.ltp_blocks_per_sm), L.ltp_block, 0, s>>>(dn, t_now, 0);
+    // sparse grids follow the net's size (a warp per spiker / per 32 buckets)
+    const int g_ltp = sized_grid(net, L.ltp_blocks_per_sm, net->N, L.ltp_block / 32);
+    const int g_del = sized_grid(net, L.deliver_blocks_per_sm, (int64_t)net->N * dn.D / 4, L.deliver_block);
+    k_ltp<<<g_ltp, L.ltp_block, 0, s>>>(dn, t_now, 0);
     mark(2);
     if (P && t > 0 && (uint32_t)t % P == 0) {
         // the long-term update needs the whole derivative: fold the
         // event-driven LTP first (both passes read sd afterwards)
         mark(3);
-        k_fold<<<grid_for(net, 8), 256, 0, s>>>(dn);
+        k_fold<<<sized_grid(net, 8, net->n_rin, 4096), 256, 0, s>>>(dn);
         k_deriv<<<dim3(deriv_grid_x(net), dn.C), L.deriv_block, 0, s>>>(dn, t_now, 0);
         mark(3);
     }
     mark(0);
-    k_deliver<<<grid_for(net, L.deliver_blocks_per_sm), L.deliver_block, 0, s>>>(dn, t_now);
+    k_deliver<<<g_del, L.deliver_block, 0, s>>>(dn, t_now);
     mark(0);
     if (net->dense_ok) {
         const uint32_t chunks = (dn.npc + dn.dense_rows - 1) / dn.dense_rows;
@@ -611,7 +636,7 @@ int build_graph(snn_net *net, int variant, uint32_t L)
     const int32_t base_t = variant ? (int32_t)net->cfg.deriv_period_ms : 0;
     cudaGraph_t g = nullptr;
     SNN_CUDA(cudaStreamBeginCapture(net->stream, cudaStreamCaptureModeThreadLocal));
-    for (uint32_t k = 0; k < L; ++k) launch_step(net, base_t + (int32_t)k);
+    for (uint32_t k = 0; k < L; ++k) launch_step(net, base_t + (int32_t)k, net->stream);
     cudaError_t e = cudaStreamEndCapture(net->stream, &g);
     if (e != cudaSuccess) {
         set_error("graph capture failed: %s", cudaGetErrorString(e));
@@ -682,7 +707,7 @@ int run_steps(snn_net *net, uint32_t n_ms)
             left -= L;
             net->ltp_owed = true;
         } else {
-            launch_step(net, t);
+            launch_step(net, t, net->stream);
             SNN_CUDA(cudaGetLastError());
             net->t += 1;
             left -= 1;
@@ -1098,6 +1123,210 @@ int snn_run_host(snn_net *net, uint32_t n_ms, const snn_stimulus *host_stimulus,
     if (k && host_spikes) std::memcpy(host_spikes, out.data(), k * sizeof(snn_spike));
     SNN_TRY(raster_reset_impl(net));
     if (trunc || out.size() > cap) { set_error("raster window truncated"); return SNN_ETRUNC; }
+    return SNN_OK;
+}
+
+void snn_batch_free(snn_batch *b)
+{
+    if (!b) return;
+    if (b->main) cudaStreamSynchronize(b->main);
+    for (int i = 0; i < 2; ++i)
+        if (b->graph[i]) cudaGraphExecDestroy(b->graph[i]);
+    for (cudaEvent_t e : b->join) cudaEventDestroy(e);
+    if (b->fork) cudaEventDestroy(b->fork);
+    for (cudaStream_t st : b->branch) cudaStreamDestroy(st);
+    if (b->main) cudaStreamDestroy(b->main);
+    delete b;
+}
+
+int snn_batch_create(snn_net *const *nets, uint32_t n_nets, uint32_t graph_steps, snn_batch **out)
+{
+    if (!out) { set_error("out is NULL"); return SNN_EINVAL; }
+    *out = nullptr;
+    if (!nets || n_nets == 0) { set_error("a batch needs at least one net"); return SNN_EINVAL; }
+    int dev = 0;
+    SNN_CUDA(cudaGetDevice(&dev));
+    const uint32_t P = nets[0]->cfg.deriv_period_ms;
+    for (uint32_t i = 0; i < n_nets; ++i) {
+        if (!nets[i]) { set_error("net %u is NULL", i); return SNN_EINVAL; }
+        if (nets[i]->device != dev) { set_error("net %u lives on another device", i); return SNN_EINVAL; }
+        if (nets[i]->cfg.deriv_period_ms != P) { set_error("nets must share deriv_period_ms"); return SNN_EINVAL; }
+        if (nets[i]->t != nets[0]->t) { set_error("nets must stand at the same step"); return SNN_ESTATE; }
+        if (nets[i]->profile) { set_error("net %u is profiling", i); return SNN_ESTATE; }
+        for (uint32_t j = 0; j < i; ++j)
+            if (nets[j] == nets[i]) { set_error("net %u appears twice", i); return SNN_EINVAL; }
+    }
+    snn_batch *b = new snn_batch();
+    auto fail = [&](int code) { snn_batch_free(b); return code; };
+    b->nets.assign(nets, nets + n_nets);
+    uint32_t L = graph_steps ? graph_steps : 10;
+    L &= ~1u;
+    if (P) {
+        while (L >= 2 && P % L) L -= 2;
+    }
+    b->L = L;
+    if (cudaStreamCreateWithFlags(&b->main, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) {
+        set_error("stream / event creation failed");
+        return fail(SNN_ECUDA);
+    }
+    b->branch.resize(n_nets, nullptr);
+    b->join.resize(n_nets, nullptr);
+    for (uint32_t i = 0; i < n_nets; ++i) {
+        if (cudaStreamCreateWithFlags(&b->branch[i], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming) != cudaSuccess) {
+            set_error("stream / event creation failed");
+            return fail(SNN_ECUDA);
+        }
+    }
+    *out = b;
+    return SNN_OK;
+}
+
+namespace {
+
+// steps [t, t + count) of every net, each on its own branch stream, joined
+// back into the batch's main stream (captured into a graph, or run eagerly)
+void batch_enqueue(snn_batch *b, int32_t t, uint32_t count)
+{
+    cudaEventRecord(b->fork, b->main);
+    for (size_t i = 0; i < b->nets.size(); ++i) {
+        cudaStreamWaitEvent(b->branch[i], b->fork, 0);
+        for (uint32_t k = 0; k < count; ++k) launch_step(b->nets[i], t + (int32_t)k, b->branch[i]);
+        cudaEventRecord(b->join[i], b->branch[i]);
+        cudaStreamWaitEvent(b->main, b->join[i], 0);
+    }
+}
+
+int batch_capture(snn_batch *b, int variant)
+{
+    if (b->graph[variant]) {
+        cudaGraphExecDestroy(b->graph[variant]);
+        b->graph[variant] = nullptr;
+    }
+    const int32_t base_t = variant ? (int32_t)b->nets[0]->cfg.deriv_period_ms : 0;
+    cudaGraph_t g = nullptr;
+    SNN_CUDA(cudaStreamBeginCapture(b->main, cudaStreamCaptureModeThreadLocal));
+    batch_enqueue(b, base_t, b->L);
+    cudaError_t e = cudaStreamEndCapture(b->main, &g);
+    if (e != cudaSuccess) { set_error("batch capture failed: %s", cudaGetErrorString(e)); return SNN_ECUDA; }
+    e = cudaGraphInstantiate(&b->graph[variant], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        b->graph[variant] = nullptr;
+        set_error("batch graph instantiate failed: %s", cudaGetErrorString(e));
+        return SNN_ECUDA;
+    }
+    b->versions[variant].clear();
+    for (snn_net *n : b->nets) b->versions[variant].push_back(n->version);
+    return SNN_OK;
+}
+
+}  // namespace
+
+int snn_batch_run(snn_batch *b, uint32_t n_ms)
+{
+    if (!b) { set_error("batch is NULL"); return SNN_EINVAL; }
+    if (n_ms == 0) return SNN_OK;
+    const int32_t t0 = b->nets[0]->t;
+    for (snn_net *n : b->nets) {
+        if (n->t != t0) { set_error("nets of the batch no longer stand at the same step"); return SNN_ESTATE; }
+        if (n->profile) { set_error("a net of the batch is profiling"); return SNN_ESTATE; }
+        if ((int64_t)n->t + n_ms > 0x7fff0000ll) { set_error("time limit reached"); return SNN_ESTATE; }
+        SNN_TRY(ensure_raster_steps(n, (int64_t)n->t + n_ms + 2 - n->dn.raster_t0));
+        SNN_CUDA(cudaStreamSynchronize(n->stream));
+    }
+    const uint32_t P = b->nets[0]->cfg.deriv_period_ms;
+    const uint32_t L = b->L;
+    int32_t t = t0;
+    uint32_t left = n_ms;
+    while (left > 0) {
+        if (L >= 2 && (uint32_t)t % L == 0 && left >= L) {
+            const int variant = (P && t > 0 && (uint32_t)t % P == 0) ? 1 : 0;
+            bool stale = !b->graph[variant];
+            for (size_t i = 0; !stale && i < b->nets.size(); ++i)
+                stale = b->versions[variant][i] != b->nets[i]->version;
+            if (stale) SNN_TRY(batch_capture(b, variant));
+            SNN_CUDA(cudaGraphLaunch(b->graph[variant], b->main));
+            t += (int32_t)L;
+            left -= L;
+        } else {
+            batch_enqueue(b, t, 1);
+            SNN_CUDA(cudaGetLastError());
+            t += 1;
+            left -= 1;
+        }
+    }
+    SNN_CUDA(cudaStreamSynchronize(b->main));
+    SNN_CUDA(cudaGetLastError());
+    int rc = SNN_OK;
+    for (snn_net *n : b->nets) {
+        n->t = t;
+        n->ltp_owed = true;
+        DevCounters hc{};
+        SNN_TRY(read_counters_raw(n, &hc));
+        if (hc.error && rc == SNN_OK) {
+            set_error("device error word %d", hc.error);
+            rc = hc.error == SNN_ETIMEOUT ? SNN_ETIMEOUT : SNN_ECUDA;
+        }
+    }
+    return rc;
+}
+
+int snn_autotune(snn_net *net, uint32_t probe_ms, snn_launch *best)
+{
+    if (!net) { set_error("net is NULL"); return SNN_EINVAL; }
+    if (net->explicit_net) { set_error("autotuning restarts the net: generated nets only"); return SNN_ESTATE; }
+    if (probe_ms == 0) probe_ms = 50;
+    const snn_launch base = net->launch;
+    std::vector<snn_launch> cand;
+    const uint32_t rows_opts[] = {0, 64, 256};
+    const uint32_t bps_opts[] = {4, 8};
+    const uint32_t nb_opts[] = {128, 256};
+    const uint32_t gs_opts[] = {10, 50};
+    for (uint32_t rows : rows_opts)
+        for (uint32_t bps : bps_opts)
+            for (uint32_t nb : nb_opts)
+                for (uint32_t gs : gs_opts) {
+                    snn_launch c = base;
+                    c.dense_rows = rows;
+                    c.deliver_blocks_per_sm = bps;
+                    c.ltp_blocks_per_sm = bps;
+                    c.neuron_block = nb;
+                    c.graph_steps = gs;
+                    cand.push_back(c);
+                }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    SNN_CUDA(cudaEventCreate(&e0));
+    SNN_CUDA(cudaEventCreate(&e1));
+    float best_ms = 1e30f;
+    size_t best_i = 0;
+    int rc = SNN_OK;
+    for (size_t i = 0; i < cand.size() && rc == SNN_OK; ++i) {
+        net->launch = cand[i];
+        net->dn.dense_min_spikes = dense_threshold(net->N, cand[i].dense_permille);
+        if ((rc = setup_dense(net)) != SNN_OK) break;
+        if (!net->dense_ok) net->dn.dense_min_spikes = 0xffffffffu;
+        drop_graphs(net);
+        if ((rc = snn_reset(net)) != SNN_OK) break;
+        cudaEventRecord(e0, net->stream);
+        if ((rc = run_steps(net, probe_ms)) != SNN_OK) break;
+        cudaEventRecord(e1, net->stream);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) { best_ms = ms; best_i = i; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != SNN_OK) return rc;
+    net->launch = cand[best_i];
+    net->dn.dense_min_spikes = dense_threshold(net->N, net->launch.dense_permille);
+    SNN_TRY(setup_dense(net));
+    if (!net->dense_ok) net->dn.dense_min_spikes = 0xffffffffu;
+    drop_graphs(net);
+    SNN_TRY(snn_reset(net));
+    if (best) *best = net->launch;
     return SNN_OK;
 }
 

@@ -166,21 +166,39 @@ __global__ void __launch_bounds__(1024) k_deliver(DevNet n, const int *t_now)
             ev_exc += (unsigned long long)exc_len;
         }
         __syncwarp();
+        // kUnroll synapses per lane in flight: weights, derivatives and
+        // targets first, then the target-side gathers, then the updates
         int j = 0;
-        for (int e = lane; e < tile_len; e += 32) {
-            while (w_start[j + 1] <= e) ++j;
-            const int64_t k = w_lo[j] + (e - w_start[j]);
-            const uint32_t inf = w_info[j];
-            const bool exc = inf & 1u;
-            const int32_t wk = n.w[k];
-            const int32_t sk = (exc && stdp) ? n.sd[k] : 0;
-            const uint32_t tg = target_gid(n, inf >> 1, k);
-            red_add(&n.I[tg], wk);
-            if (exc && stdp) {
-                const int lag = t - n.last_spike[tg];          // >= 1
+        for (int e0 = lane; e0 < tile_len; e0 += 32 * kUnroll) {
+            int64_t k[kUnroll];
+            uint32_t inf[kUnroll], tg[kUnroll];
+            int32_t wk[kUnroll], sk[kUnroll], ls[kUnroll];
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+                const int e = e0 + 32 * u;
+                k[u] = -1;
+                if (e < tile_len) {
+                    while (w_start[j + 1] <= e) ++j;
+                    k[u] = w_lo[j] + (e - w_start[j]);
+                    inf[u] = w_info[j];
+                    wk[u] = n.w[k[u]];
+                    sk[u] = ((inf[u] & 1u) && stdp) ? n.sd[k[u]] : 0;
+                    tg[u] = target_gid(n, inf[u] >> 1, k[u]);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+                if (k[u] < 0) continue;
+                red_add(&n.I[tg[u]], wk[u]);
+                ls[u] = ((inf[u] & 1u) && stdp) ? n.last_spike[tg[u]] : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+                if (k[u] < 0 || !((inf[u] & 1u) && stdp)) continue;
+                const int lag = t - ls[u];                     // >= 1
                 if (lag < kLut) {
                     const int32_t a = s_lut[lag];
-                    if (a) n.sd[k] = sk - a;
+                    if (a) n.sd[k[u]] = sk[u] - a;
                 }
             }
         }

@@ -110,6 +110,10 @@ _SIGS = {
     "snn_save_state": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t, _P(ctypes.c_size_t)]),
     "snn_load_state": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t]),
     "snn_reset": (ctypes.c_int, [_vp]),
+    "snn_autotune": (ctypes.c_int, [_vp, ctypes.c_uint32, _P(SnnLaunch)]),
+    "snn_batch_create": (ctypes.c_int, [_vp, ctypes.c_uint32, ctypes.c_uint32, _P(_vp)]),
+    "snn_batch_run": (ctypes.c_int, [_vp, ctypes.c_uint32]),
+    "snn_batch_free": (None, [_vp]),
     "snn_thalamic_events": (ctypes.c_int, [_P(SnnConfig), ctypes.c_int32, ctypes.c_uint32, _vp, ctypes.c_size_t,
                                            _P(ctypes.c_size_t)]),
     "snn_free": (None, [_vp]),
@@ -319,6 +323,12 @@ class Network:
     def set_thalamic(self, on: bool):
         _check(self._lib.snn_set_thalamic(self.h, int(bool(on))), "snn_set_thalamic")
 
+    def autotune(self, probe_ms: int = 50) -> dict:
+        """Pick the fastest launch shape (the net is left reset at t = 0)."""
+        L = SnnLaunch()
+        _check(self._lib.snn_autotune(self.h, int(probe_ms), ctypes.byref(L)), "snn_autotune")
+        return {k: getattr(L, k) for k, _ in SnnLaunch._fields_}
+
     def reset(self):
         _check(self._lib.snn_reset(self.h), "snn_reset")
 
@@ -409,3 +419,36 @@ class Network:
     def load_state(self, data: bytes):
         buf = ctypes.create_string_buffer(data, len(data))
         _check(self._lib.snn_load_state(self.h, buf, len(data)), "snn_load_state")
+
+
+class Batch:
+    """Many independent nets advanced together by one CUDA graph per chunk of
+    steps (each net a parallel branch).  Does not own the nets."""
+
+    def __init__(self, nets, graph_steps: int = 10):
+        self._lib = load()
+        self.nets = list(nets)
+        arr = (ctypes.c_void_p * len(self.nets))(*[n.h.value for n in self.nets])
+        self.h = ctypes.c_void_p()
+        _check(self._lib.snn_batch_create(arr, len(self.nets), int(graph_steps), ctypes.byref(self.h)),
+               "snn_batch_create")
+
+    def run(self, n_ms: int):
+        _check(self._lib.snn_batch_run(self.h, int(n_ms)), "snn_batch_run")
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self._lib.snn_batch_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,131 @@
+"""Batches of independent uneven networks and the launch-shape autotuner:
+every net of a batch must evolve exactly as it does alone (and as the
+oracle), whatever the graph chunking, tails and launch shapes."""
+import numpy as np
+import pytest
+
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def eng():
+    import paper_1310_8478_gb300 as e
+    e.build_engine()
+    return e
+
+
+def _small_mix():
+    cfgs = workloads.batch_workloads(n=6, side=(1, 3), fanouts=(60, 100, 400), draw_seed=7)
+    assert len({(c["grid_x"], c["fanout"]) for c in cfgs}) > 2     # really uneven
+    return cfgs
+
+
+def _net(eng, c, T):
+    return eng.Network(c, raster_capacity=workloads.n_neurons(c) * T + 1024)
+
+
+def _state(net):
+    t, g = net.raster()
+    w, sd = net.weights()
+    return t, g, w, sd, net.counters()["e_all"]
+
+
+def _same(a, b):
+    for x, y in zip(a[:4], b[:4]):
+        assert np.array_equal(x, y)
+    assert a[4] == b[4]
+
+
+@pytest.mark.parametrize("graph_steps,T", [(10, 1100), (4, 1003), (50, 1050)])
+def test_batch_equals_nets_run_alone(eng, graph_steps, T):
+    cfgs = _small_mix()
+    alone = []
+    for c in cfgs:
+        with _net(eng, c, T) as n:
+            n.run(T)
+            alone.append(_state(n))
+    nets = [_net(eng, c, T) for c in cfgs]
+    try:
+        with eng.Batch(nets, graph_steps=graph_steps) as b:
+            b.run(7)                 # a tail before the first aligned chunk
+            b.run(T - 7)
+        for n, ref in zip(nets, alone):
+            assert n.counters()["t"] == T
+            _same(_state(n), ref)
+    finally:
+        for n in nets:
+            n.close()
+
+
+def test_batch_equals_oracle(eng, orc):
+    # low fan-outs keep the oracle fast; the uneven batch above covers M = 400
+    cfgs = [workloads.custom(grid_x=1, grid_y=1, fanout=100, seed=1101),
+            workloads.custom(grid_x=2, grid_y=2, fanout=60, pct_ring=(40, 30, 20, 10), seed=1102),
+            workloads.custom(grid_x=3, grid_y=2, fanout=40, pct_ring=(40, 30, 20, 10), seed=1103)]
+    nets = [_net(eng, c, 1020) for c in cfgs]
+    try:
+        with eng.Batch(nets, graph_steps=10) as b:
+            b.run(1020)
+        for c, n in zip(cfgs, nets):
+            o = orc.Oracle(c)
+            o.run(1020)
+            ot, og = o.raster()
+            gt, gg = n.raster()
+            assert np.array_equal(ot, gt) and np.array_equal(og, gg)
+            s = o.synapses()
+            w, sd = n.weights()
+            assert np.array_equal(s["w"], w) and np.array_equal(s["sd"], sd)
+    finally:
+        for n in nets:
+            n.close()
+
+
+def test_batch_refuses_nets_at_different_steps(eng):
+    cfgs = _small_mix()[:2]
+    nets = [eng.Network(c, raster_capacity=1 << 20) for c in cfgs]
+    try:
+        nets[0].run(3)
+        with pytest.raises(eng.SnnError) as e:
+            eng.Batch(nets)
+        assert e.value.code == -7
+    finally:
+        for n in nets:
+            n.close()
+
+
+def test_batch_recaptures_after_a_net_changes(eng):
+    cfgs = _small_mix()[:3]
+    alone = []
+    for c in cfgs:
+        with _net(eng, c, 400) as n:
+            n.run(200)
+            n.set_launch(dense_permille=1)
+            n.run(200)
+            alone.append(_state(n))
+    nets = [_net(eng, c, 400) for c in cfgs]
+    try:
+        with eng.Batch(nets, graph_steps=10) as b:
+            b.run(200)
+            for n in nets:
+                n.set_launch(dense_permille=1)
+            b.run(200)
+        for n, ref in zip(nets, alone):
+            _same(_state(n), ref)
+    finally:
+        for n in nets:
+            n.close()
+
+
+def test_autotune_keeps_results(eng):
+    cfg = workloads.custom(grid_x=3, grid_y=2, fanout=400, pct_ring=(40, 30, 20, 10), seed=91)
+    with _net(eng, cfg, 1100) as ref:
+        ref.run(1010)
+        r = _state(ref)
+    with _net(eng, cfg, 1100) as n:
+        n.run(37)
+        shape = n.autotune(probe_ms=20)
+        assert n.counters()["t"] == 0 and shape["graph_steps"] in (10, 50)
+        n.run(1010)
+        _same(_state(n), r)

@@ -89,3 +89,21 @@ def n_neurons(cfg: dict) -> int:
 
 def n_synapses(cfg: dict) -> int:
     return n_neurons(cfg) * cfg["fanout"]
+
+
+def batch_workloads(n: int = 256, first_seed: int = 1000, side=(1, 16), fanouts=(100, 400, 1125),
+                    draw_seed: int = 2024, sim_ms: int = 1000) -> list:
+    """Independent uneven networks: grid side uniform in [side], fan-out uniform
+    over `fanouts`, network seeds first_seed, first_seed + 1, ...; the sizes
+    are drawn from a fixed numpy generator (draw_seed) so the list is the same
+    every time."""
+    import numpy as np
+    rng = np.random.default_rng(draw_seed)
+    out = []
+    for i in range(n):
+        sd = int(rng.integers(side[0], side[1] + 1))
+        m = int(fanouts[int(rng.integers(0, len(fanouts)))])
+        mix = (40, 30, 20, 10) if sd > 1 else (100, 0, 0, 0)
+        out.append(custom(grid_x=sd, grid_y=sd, fanout=m, pct_ring=mix, seed=first_seed + i, sim_ms=sim_ms,
+                          name="batch%03d_%dx%d_m%d" % (i, sd, sd, m)))
+    return out
