@@ -48,6 +48,12 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="bound of the oracle sample")
     ap.add_argument("--ref-budget-s", type=float, default=150.0, help="wall bound of the reference arm")
     ap.add_argument("--no-small", action="store_true", help="skip the 1-column latency line")
+    ap.add_argument("--batch-bench", type=int, default=0, metavar="NETS",
+                    help="instead: the uneven batched workload (first NETS of 256 nets), batched vs one at a time")
+    ap.add_argument("--batch-budget-gb", type=float, default=150.0, help="device budget of one wave of nets")
+    ap.add_argument("--serve-bench", type=int, default=0, metavar="REQUESTS",
+                    help="instead: the serving workload (Poisson arrivals) with this many requests")
+    ap.add_argument("--serve-rate", type=float, default=200.0, help="mean arrivals per second")
     return ap.parse_args()
 
 
@@ -199,10 +205,111 @@ def measured_peaks():
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
+def run_batch_bench(args):
+    """Independent uneven networks (grid side 1..16, M in {100, 400, 1125},
+    seeds 1000..): every wave of nets that fits the budget advances --steps
+    steps twice from the initial state, once one net after another (each with
+    its own CUDA graphs) and once as one batch (one graph per chunk, nets on
+    parallel branches); throughput = synaptic events / device time."""
+    import torch
+    import paper_1310_8478_gb300 as eng
+    torch.cuda.set_device(0)
+    eng.build_engine()
+    cfgs = workloads.batch_workloads()[: args.batch_bench]
+    T = args.steps
+    budget = int(args.batch_budget_gb * 1e9)
+    stream = torch.cuda.Stream()
+    seq_s = bat_s = 0.0
+    seq_ev = bat_ev = 0
+    waves = 0
+    i = 0
+    with torch.cuda.stream(stream):
+        while i < len(cfgs):
+            wave, used = [], 0
+            while i < len(cfgs):
+                n = eng.Network(cfgs[i], stream=stream, raster_capacity=0)
+                if wave and used + n.device_bytes > budget:
+                    n.close()
+                    break
+                wave.append(n)
+                used += n.device_bytes
+                i += 1
+            waves += 1
+            # one at a time
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for n in wave:
+                n.run(T)
+            torch.cuda.synchronize()
+            seq_s += time.perf_counter() - t0
+            seq_ev += sum(n.counters()["e_all"] for n in wave)
+            for n in wave:
+                n.reset()
+            # batched
+            with eng.Batch(wave, graph_steps=10) as b:
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                b.run(T)
+                torch.cuda.synchronize()
+                bat_s += time.perf_counter() - t0
+            bat_ev += sum(n.counters()["e_all"] for n in wave)
+            for n in wave:
+                n.close()
+    line = {"metric": "synaptic events/s", "mode": "batch", "unit": "events/s", "n_gpus": 1,
+            "nets": len(cfgs), "waves": waves, "steps": T, "raster": "off",
+            "config": {"workload": "%d independent nets, grid side uniform 1..16, M in {100, 400, 1125}, "
+                                   "seeds 1000.., wave budget %.0f GB" % (len(cfgs), args.batch_budget_gb)},
+            "value": bat_ev / bat_s, "batched_s": bat_s, "one_at_a_time": seq_ev / seq_s,
+            "one_at_a_time_s": seq_s, "speedup": (bat_ev / bat_s) / (seq_ev / seq_s),
+            "same_events": seq_ev == bat_ev, "events": bat_ev}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serve_bench(args):
+    """Simulation requests arriving as a Poisson stream (mean --serve-rate per
+    second; grid side log-uniform 1..32, M in {100, 400, 1125}, duration
+    uniform 100..5000 ms, seeds 5000..) served with continuous batching under
+    the --batch-budget-gb device budget; latency = completion - arrival."""
+    import torch
+    import paper_1310_8478_gb300 as eng
+    from paper_1310_8478_gb300 import serve
+    torch.cuda.set_device(0)
+    eng.build_engine()
+    params = {}
+
+    def cfg_of(i, rng):
+        c, d = workloads.serve_request_params(i, rng)
+        params[i] = d
+        return c
+
+    reqs = serve.poisson_requests(args.serve_bench, args.serve_rate, cfg_of, lambda i, rng: params[i])
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        srv = serve.Server(int(args.batch_budget_gb * 1e9), chunk_ms=10, stream=stream)
+        t0 = time.perf_counter()
+        res = srv.serve(reqs)
+        wall = time.perf_counter() - t0
+    ev = sum(r.events for r in res)
+    line = {"metric": "synaptic events/s", "mode": "serve", "unit": "events/s", "n_gpus": 1,
+            "requests": len(res), "rate_per_s": args.serve_rate, "budget_gb": args.batch_budget_gb,
+            "config": {"workload": "Poisson requests, grid side log-uniform 1..32, M in {100, 400, 1125}, "
+                                   "duration uniform 100..5000 ms, seeds 5000.."},
+            "value": ev / wall, "wall_s": wall, "events": ev, "latency": serve.latency_stats(res),
+            "chunks": srv.chunks, "rebatches": srv.rebatches,
+            "sim_ms_total": int(sum(r.steps for r in res))}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.batch_bench:
+        return run_batch_bench(args)
+    if args.serve_bench:
+        return run_serve_bench(args)
     rank, local_rank, world = dist_env()
     import torch
     import paper_1310_8478_gb300 as eng

@@ -301,13 +301,14 @@ int snn_autotune(snn_net *net, uint32_t probe_ms, snn_launch *best);
  * every net it holds with one CUDA-graph launch per chunk of graph_steps
  * steps; each net's kernels form a parallel branch of the graph, so small,
  * launch-bound nets run concurrently instead of one after another.  Each net
- * keeps its own state, stream-independent and bit-identical to running it
- * alone.  The batch owns no net: free the batch before its nets.  All nets
- * must be on the current device, share deriv_period_ms, have profiling off
- * and stand at the same step t.
+ * keeps its own state and step count (nets may stand at different steps and
+ * have different periods), bit-identical to running it alone.  The batch
+ * owns no net: free the batch before its nets.  All nets must be on the
+ * current device and have profiling off.  A change to any net (stimulus,
+ * launch shape, raster reset) makes the batch capture its graph again.
  *   graph_steps: steps per captured chunk (even; 0 = 10).
- * Errors: SNN_EINVAL (empty list, mismatched period), SNN_ESTATE (different
- * t), SNN_ECUDA.
+ * Errors: SNN_EINVAL (empty list, a net twice), SNN_ESTATE (profiling),
+ * SNN_ECUDA.
  */
 typedef struct snn_batch snn_batch;
 int snn_batch_create(snn_net *const *nets, uint32_t n_nets, uint32_t graph_steps, snn_batch **out);

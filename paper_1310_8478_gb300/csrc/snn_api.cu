@@ -134,8 +134,9 @@ struct snn_batch {
     cudaEvent_t fork = nullptr;
     std::vector<cudaEvent_t> join;
     uint32_t L = 0;
-    cudaGraphExec_t graph[2] = {nullptr, nullptr};
-    std::vector<uint64_t> versions[2];   // the nets' versions when each graph was captured
+    cudaGraphExec_t graph = nullptr;
+    std::vector<uint64_t> versions;      // the nets' versions when the graph was captured
+    std::vector<int> parity;             // the nets' step parity when the graph was captured
 };
 
 namespace {
@@ -548,13 +549,6 @@ cudaEvent_t next_event(snn_net *net, int kind)
     return net->ev_pool[net->ev_used++];
 }
 
-int deriv_grid_x(const snn_net *net)
-{
-    const DevNet &dn = net->dn;
-    const int64_t per_col = dn.uniform_m ? (int64_t)dn.ne * dn.uniform_m
-                                         : net->S_store / std::max<uint32_t>(1u, dn.C) + 1;
-    return (int)std::min<int64_t>(1024, std::max<int64_t>(1, per_col / ((int64_t)net->launch.deriv_block * 4)));
-}
 
 // the LTP (and long-term update) owed by step t - 1, applied before any read
 void launch_flush(snn_net *net)
@@ -564,10 +558,11 @@ void launch_flush(snn_net *net)
     const int32_t t = net->t;
     const int *t_now = &net->ctr->t_slot[t & 1];
     k_ltp<<<grid_for(net, net->launch.ltp_blocks_per_sm), net->launch.ltp_block, 0, s>>>(dn, t_now, 1);
-    k_fold<<<sized_grid(net, 8, net->n_rin, 4096), 256, 0, s>>>(dn);
+    k_fold<<<sized_grid(net, 8, net->n_rin, 4096), 256, 0, s>>>(dn, t_now, 1);
     const uint32_t P = net->cfg.deriv_period_ms;
     if (P && t > 0 && (uint32_t)t % P == 0)
-        k_deriv<<<dim3(deriv_grid_x(net), dn.C), net->launch.deriv_block, 0, s>>>(dn, t_now, 1);
+        k_deriv<<<sized_grid(net, 8, (int64_t)dn.C * dn.ne, net->launch.deriv_block / 32), net->launch.deriv_block, 0,
+                  s>>>(dn, t_now, 1);
     const int32_t none = kNoPending;
     cudaMemcpyAsync(&net->ctr->ltp_pending, &none, sizeof none, cudaMemcpyHostToDevice, s);
 }
@@ -580,6 +575,7 @@ void launch_step(snn_net *net, int32_t t, cudaStream_t s)
     const snn_launch &L = net->launch;
     const bool prof = net->profile;
     const uint32_t P = net->cfg.deriv_period_ms;
+    (void)P;
     auto mark = [&](int kind) {
         if (prof) cudaEventRecord(next_event(net, kind), s);
     };
@@ -591,12 +587,13 @@ void launch_step(snn_net *net, int32_t t, cudaStream_t s)
     const int g_del = sized_grid(net, L.deliver_blocks_per_sm, (int64_t)net->N * dn.D / 4, L.deliver_block);
     k_ltp<<<g_ltp, L.ltp_block, 0, s>>>(dn, t_now, 0);
     mark(2);
-    if (P && t > 0 && (uint32_t)t % P == 0) {
-        // the long-term update needs the whole derivative: fold the
-        // event-driven LTP first (both passes read sd afterwards)
+    // long-term update when t closes a period (decided on the device, so the
+    // same launches serve every step and graphs need no variants): the
+    // event-driven LTP is folded into sd first, both passes read sd afterwards
+    if (P) {
         mark(3);
-        k_fold<<<sized_grid(net, 8, net->n_rin, 4096), 256, 0, s>>>(dn);
-        k_deriv<<<dim3(deriv_grid_x(net), dn.C), L.deriv_block, 0, s>>>(dn, t_now, 0);
+        k_fold<<<sized_grid(net, 8, net->n_rin, 4096), 256, 0, s>>>(dn, t_now, 0);
+        k_deriv<<<sized_grid(net, 8, (int64_t)dn.C * dn.ne, L.deriv_block / 32), L.deriv_block, 0, s>>>(dn, t_now, 0);
         mark(3);
     }
     mark(0);
@@ -618,34 +615,27 @@ void launch_step(snn_net *net, int32_t t, cudaStream_t s)
 
 uint32_t effective_graph_len(const snn_net *net)
 {
-    uint32_t L = net->launch.graph_steps;
+    const uint32_t L = net->launch.graph_steps;
     if (net->profile || L < 2) return 0;
-    const uint32_t P = net->cfg.deriv_period_ms;
-    if (P == 0) return L & ~1u;
-    for (uint32_t l = std::min(L, P) & ~1u; l >= 2; l -= 2)
-        if (P % l == 0) return l;
-    return 0;
+    return L & ~1u;
 }
 
-// variant 1: the chunk's first step closes a plasticity period (its k_deriv
-// launch is part of the graph)
-int build_graph(snn_net *net, int variant, uint32_t L)
+// one chunk of L steps starting at an even step (only the parity of t is
+// baked into the launches; everything else is read on the device)
+int build_graph(snn_net *net, uint32_t L)
 {
-    // steps t0 .. t0+L-1 with t0 = P (variant 1) or 0 (no positive multiple of
-    // P inside, as L divides P); only the parity of t and t mod P matter
-    const int32_t base_t = variant ? (int32_t)net->cfg.deriv_period_ms : 0;
     cudaGraph_t g = nullptr;
     SNN_CUDA(cudaStreamBeginCapture(net->stream, cudaStreamCaptureModeThreadLocal));
-    for (uint32_t k = 0; k < L; ++k) launch_step(net, base_t + (int32_t)k, net->stream);
+    for (uint32_t k = 0; k < L; ++k) launch_step(net, (int32_t)k, net->stream);
     cudaError_t e = cudaStreamEndCapture(net->stream, &g);
     if (e != cudaSuccess) {
         set_error("graph capture failed: %s", cudaGetErrorString(e));
         return SNN_ECUDA;
     }
-    e = cudaGraphInstantiate(&net->graph[variant], g, 0);
+    e = cudaGraphInstantiate(&net->graph[0], g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {
-        net->graph[variant] = nullptr;
+        net->graph[0] = nullptr;
         set_error("graph instantiate failed: %s", cudaGetErrorString(e));
         return SNN_ECUDA;
     }
@@ -685,7 +675,6 @@ int run_steps(snn_net *net, uint32_t n_ms)
 {
     if ((int64_t)net->t + n_ms > 0x7fff0000ll) { set_error("time limit reached"); return SNN_ESTATE; }
     SNN_TRY(ensure_raster_steps(net, (int64_t)net->t + n_ms + 2 - net->dn.raster_t0));
-    const uint32_t P = net->cfg.deriv_period_ms;
     const uint32_t L = effective_graph_len(net);
     if (L != net->graph_len) {
         drop_graphs(net);
@@ -694,15 +683,14 @@ int run_steps(snn_net *net, uint32_t n_ms)
     uint32_t left = n_ms;
     while (left > 0) {
         const int32_t t = net->t;
-        if (L >= 2 && (uint32_t)t % L == 0 && left >= L) {
-            const int variant = (P && t > 0 && (uint32_t)t % P == 0) ? 1 : 0;
+        if (L >= 2 && (t & 1) == 0 && left >= L) {
             if (net->graphs_dirty) {
                 for (int i = 0; i < 2; ++i)
                     if (net->graph[i]) { cudaGraphExecDestroy(net->graph[i]); net->graph[i] = nullptr; }
                 net->graphs_dirty = false;
             }
-            if (!net->graph[variant]) SNN_TRY(build_graph(net, variant, L));
-            SNN_CUDA(cudaGraphLaunch(net->graph[variant], net->stream));
+            if (!net->graph[0]) SNN_TRY(build_graph(net, L));
+            SNN_CUDA(cudaGraphLaunch(net->graph[0], net->stream));
             net->t += (int32_t)L;
             left -= L;
             net->ltp_owed = true;
@@ -1130,8 +1118,7 @@ void snn_batch_free(snn_batch *b)
 {
     if (!b) return;
     if (b->main) cudaStreamSynchronize(b->main);
-    for (int i = 0; i < 2; ++i)
-        if (b->graph[i]) cudaGraphExecDestroy(b->graph[i]);
+    if (b->graph) cudaGraphExecDestroy(b->graph);
     for (cudaEvent_t e : b->join) cudaEventDestroy(e);
     if (b->fork) cudaEventDestroy(b->fork);
     for (cudaStream_t st : b->branch) cudaStreamDestroy(st);
@@ -1146,12 +1133,9 @@ int snn_batch_create(snn_net *const *nets, uint32_t n_nets, uint32_t graph_steps
     if (!nets || n_nets == 0) { set_error("a batch needs at least one net"); return SNN_EINVAL; }
     int dev = 0;
     SNN_CUDA(cudaGetDevice(&dev));
-    const uint32_t P = nets[0]->cfg.deriv_period_ms;
     for (uint32_t i = 0; i < n_nets; ++i) {
         if (!nets[i]) { set_error("net %u is NULL", i); return SNN_EINVAL; }
         if (nets[i]->device != dev) { set_error("net %u lives on another device", i); return SNN_EINVAL; }
-        if (nets[i]->cfg.deriv_period_ms != P) { set_error("nets must share deriv_period_ms"); return SNN_EINVAL; }
-        if (nets[i]->t != nets[0]->t) { set_error("nets must stand at the same step"); return SNN_ESTATE; }
         if (nets[i]->profile) { set_error("net %u is profiling", i); return SNN_ESTATE; }
         for (uint32_t j = 0; j < i; ++j)
             if (nets[j] == nets[i]) { set_error("net %u appears twice", i); return SNN_EINVAL; }
@@ -1159,12 +1143,7 @@ int snn_batch_create(snn_net *const *nets, uint32_t n_nets, uint32_t graph_steps
     snn_batch *b = new snn_batch();
     auto fail = [&](int code) { snn_batch_free(b); return code; };
     b->nets.assign(nets, nets + n_nets);
-    uint32_t L = graph_steps ? graph_steps : 10;
-    L &= ~1u;
-    if (P) {
-        while (L >= 2 && P % L) L -= 2;
-    }
-    b->L = L;
+    b->L = (graph_steps ? graph_steps : 10) & ~1u;
     if (cudaStreamCreateWithFlags(&b->main, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) {
         set_error("stream / event creation failed");
@@ -1185,40 +1164,45 @@ int snn_batch_create(snn_net *const *nets, uint32_t n_nets, uint32_t graph_steps
 
 namespace {
 
-// steps [t, t + count) of every net, each on its own branch stream, joined
-// back into the batch's main stream (captured into a graph, or run eagerly)
-void batch_enqueue(snn_batch *b, int32_t t, uint32_t count)
+// the next `count` steps of every net (from its own t), each net on its own
+// branch stream, joined back into the batch's main stream (captured into a
+// graph, or run eagerly)
+void batch_enqueue(snn_batch *b, uint32_t count)
 {
     cudaEventRecord(b->fork, b->main);
     for (size_t i = 0; i < b->nets.size(); ++i) {
+        snn_net *n = b->nets[i];
         cudaStreamWaitEvent(b->branch[i], b->fork, 0);
-        for (uint32_t k = 0; k < count; ++k) launch_step(b->nets[i], t + (int32_t)k, b->branch[i]);
+        for (uint32_t k = 0; k < count; ++k) launch_step(n, n->t + (int32_t)k, b->branch[i]);
         cudaEventRecord(b->join[i], b->branch[i]);
         cudaStreamWaitEvent(b->main, b->join[i], 0);
     }
 }
 
-int batch_capture(snn_batch *b, int variant)
+int batch_capture(snn_batch *b)
 {
-    if (b->graph[variant]) {
-        cudaGraphExecDestroy(b->graph[variant]);
-        b->graph[variant] = nullptr;
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
     }
-    const int32_t base_t = variant ? (int32_t)b->nets[0]->cfg.deriv_period_ms : 0;
     cudaGraph_t g = nullptr;
     SNN_CUDA(cudaStreamBeginCapture(b->main, cudaStreamCaptureModeThreadLocal));
-    batch_enqueue(b, base_t, b->L);
+    batch_enqueue(b, b->L);
     cudaError_t e = cudaStreamEndCapture(b->main, &g);
     if (e != cudaSuccess) { set_error("batch capture failed: %s", cudaGetErrorString(e)); return SNN_ECUDA; }
-    e = cudaGraphInstantiate(&b->graph[variant], g, 0);
+    e = cudaGraphInstantiate(&b->graph, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {
-        b->graph[variant] = nullptr;
+        b->graph = nullptr;
         set_error("batch graph instantiate failed: %s", cudaGetErrorString(e));
         return SNN_ECUDA;
     }
-    b->versions[variant].clear();
-    for (snn_net *n : b->nets) b->versions[variant].push_back(n->version);
+    b->versions.clear();
+    b->parity.clear();
+    for (snn_net *n : b->nets) {
+        b->versions.push_back(n->version);
+        b->parity.push_back(n->t & 1);
+    }
     return SNN_OK;
 }
 
@@ -1228,32 +1212,28 @@ int snn_batch_run(snn_batch *b, uint32_t n_ms)
 {
     if (!b) { set_error("batch is NULL"); return SNN_EINVAL; }
     if (n_ms == 0) return SNN_OK;
-    const int32_t t0 = b->nets[0]->t;
     for (snn_net *n : b->nets) {
-        if (n->t != t0) { set_error("nets of the batch no longer stand at the same step"); return SNN_ESTATE; }
         if (n->profile) { set_error("a net of the batch is profiling"); return SNN_ESTATE; }
         if ((int64_t)n->t + n_ms > 0x7fff0000ll) { set_error("time limit reached"); return SNN_ESTATE; }
         SNN_TRY(ensure_raster_steps(n, (int64_t)n->t + n_ms + 2 - n->dn.raster_t0));
         SNN_CUDA(cudaStreamSynchronize(n->stream));
     }
-    const uint32_t P = b->nets[0]->cfg.deriv_period_ms;
     const uint32_t L = b->L;
-    int32_t t = t0;
     uint32_t left = n_ms;
     while (left > 0) {
-        if (L >= 2 && (uint32_t)t % L == 0 && left >= L) {
-            const int variant = (P && t > 0 && (uint32_t)t % P == 0) ? 1 : 0;
-            bool stale = !b->graph[variant];
+        if (L >= 2 && left >= L) {
+            // the graph holds each net's launches for its step parity at capture
+            bool stale = !b->graph;
             for (size_t i = 0; !stale && i < b->nets.size(); ++i)
-                stale = b->versions[variant][i] != b->nets[i]->version;
-            if (stale) SNN_TRY(batch_capture(b, variant));
-            SNN_CUDA(cudaGraphLaunch(b->graph[variant], b->main));
-            t += (int32_t)L;
+                stale = b->versions[i] != b->nets[i]->version || b->parity[i] != (b->nets[i]->t & 1);
+            if (stale) SNN_TRY(batch_capture(b));
+            SNN_CUDA(cudaGraphLaunch(b->graph, b->main));
+            for (snn_net *n : b->nets) n->t += (int32_t)L;
             left -= L;
         } else {
-            batch_enqueue(b, t, 1);
+            batch_enqueue(b, 1);
             SNN_CUDA(cudaGetLastError());
-            t += 1;
+            for (snn_net *n : b->nets) n->t += 1;
             left -= 1;
         }
     }
@@ -1261,7 +1241,6 @@ int snn_batch_run(snn_batch *b, uint32_t n_ms)
     SNN_CUDA(cudaGetLastError());
     int rc = SNN_OK;
     for (snn_net *n : b->nets) {
-        n->t = t;
         n->ltp_owed = true;
         DevCounters hc{};
         SNN_TRY(read_counters_raw(n, &hc));

@@ -255,7 +255,7 @@ __global__ void k_dense(DevNet n, const int *t_now);
 __global__ void k_neuron(DevNet n, const int *t_now, int *t_next);
 __global__ void k_ltp(DevNet n, const int *t_now, int force);
 __global__ void k_deriv(DevNet n, const int *t_now, int force);
-__global__ void k_fold(DevNet n);
+__global__ void k_fold(DevNet n, const int *t_now, int force);
 
 size_t dense_smem_bytes(uint32_t npc, uint32_t block);
 

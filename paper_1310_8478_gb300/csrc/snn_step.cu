@@ -271,8 +271,12 @@ __global__ void __launch_bounds__(1024) k_ltp(DevNet n, const int *t_now, int fo
 // fold the event-driven LTP accumulated in reverse order into the forward
 // derivatives (each forward excitatory synapse has exactly one reverse entry)
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_fold(DevNet n)
+__global__ void __launch_bounds__(1024) k_fold(DevNet n, const int *t_now, int force)
 {
+    if (!force) {
+        const int t = *t_now;        // only before a long-term update (t closes a period)
+        if (!n.deriv_period || t <= 0 || (t % (int)n.deriv_period) != 0) return;
+    }
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n.n_rin; e += stride) {
         const int32_t v = n.sd_rev[e];
@@ -284,38 +288,30 @@ __global__ void __launch_bounds__(1024) k_fold(DevNet n)
 }
 
 // ---------------------------------------------------------------------------
-// sparse S5 closing step t - 1 (when t is a multiple of the period): over the
-// excitatory rows of column blockIdx.y (rows c*npc .. c*npc+ne-1 are
-// contiguous): w = clamp(w + bias + sd, 0, wmax), sd = (sd*decay + 2^15) >> 16.
+// sparse S5 closing step t - 1 (when t is a multiple of the period): warp per
+// excitatory row (grid-stride, so a step that closes no period costs one tiny
+// launch): w = clamp(w + bias + sd, 0, wmax), sd = (sd*decay + 2^15) >> 16.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024) k_deriv(DevNet n, const int *t_now, int force)
 {
     const int t = *t_now;
+    if (!n.deriv_period || t <= 0 || (t % (int)n.deriv_period) != 0) return;
     if (n.ctr->ltp_pending != t - 1) return;
     if (!force && dense_selected(n, t)) return;
-    const uint32_t col = blockIdx.y;
-    const int64_t lo = row_base(n, col * n.npc);
-    const int64_t hi = n.uniform_m ? (int64_t)(col * n.npc + n.ne) * n.uniform_m
-                                   : n.row_off[col * n.npc + n.ne];
-    for (int64_t k = lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < hi;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t s = n.sd[k];
-        n.w[k] = deriv_w(n, n.w[k], s);
-        n.sd[k] = deriv_sd(n, s);
+    const int lane = threadIdx.x & 31;
+    const uint32_t rows = n.C * n.ne;
+    const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < rows; r += warps) {
+        const uint32_t p = (r / n.ne) * n.npc + (r % n.ne);
+        const int64_t lo = row_base(n, p), hi = lo + row_len(n, p);
+        for (int64_t k = lo + lane; k < hi; k += 32) {
+            const int32_t s = n.sd[k];
+            n.w[k] = deriv_w(n, n.w[k], s);
+            n.sd[k] = deriv_sd(n, s);
+        }
     }
 }
 
-// ---------------------------------------------------------------------------
-// dense [S4(t-1) S5(t-1) S1(t)] for compact nets.  Block = (column c, chunk of
-// dense_rows source rows of c).  Shared memory holds, for the 13 columns the
-// rows can reach (slots), the Q16 input accumulated by this block and the lag
-// t - last_spike of every neuron (saturated at 255; lag 1 <=> fired at t-1).
-// Warp per row; lanes walk the row's positions in order; every position's
-// delay bucket gives its per-bucket flags (deliver: the source fired at t - d;
-// LTP amount: from the source's history at t - 1).  Per synapse, in order:
-// sd += LTP amount if the target fired at t - 1; the long-term update if the
-// period ended at t - 1; delivery into the staged input and LTD.  The staged
-// input is flushed with one reduction per neuron touched.
 // ---------------------------------------------------------------------------
 size_t dense_smem_bytes(uint32_t npc, uint32_t block)
 {

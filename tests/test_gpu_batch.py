@@ -82,14 +82,28 @@ def test_batch_equals_oracle(eng, orc):
             n.close()
 
 
-def test_batch_refuses_nets_at_different_steps(eng):
-    cfgs = _small_mix()[:2]
-    nets = [eng.Network(c, raster_capacity=1 << 20) for c in cfgs]
+def test_batch_of_nets_at_different_steps(eng):
+    # continuous batching: nets join at different times; each keeps its own
+    # clock, long-term updates happen at its own period boundaries
+    cfgs = _small_mix()[:3]
+    starts = [0, 3, 517]
+    T = 1000
+    alone = []
+    for c, s0 in zip(cfgs, starts):
+        with _net(eng, c, s0 + T) as n:
+            n.run(s0 + T)
+            alone.append(_state(n))
+    nets = [_net(eng, c, s0 + T) for c, s0 in zip(cfgs, starts)]
     try:
-        nets[0].run(3)
-        with pytest.raises(eng.SnnError) as e:
-            eng.Batch(nets)
-        assert e.value.code == -7
+        for n, s0 in zip(nets, starts):
+            n.run(s0)
+        with eng.Batch(nets, graph_steps=10) as b:
+            b.run(T)
+        for n, s0, ref in zip(nets, starts, alone):
+            assert n.counters()["t"] == s0 + T
+            _same(_state(n), ref)
+        with pytest.raises(eng.SnnError):
+            eng.Batch([nets[0], nets[0]])
     finally:
         for n in nets:
             n.close()

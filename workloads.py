@@ -107,3 +107,19 @@ def batch_workloads(n: int = 256, first_seed: int = 1000, side=(1, 16), fanouts=
         out.append(custom(grid_x=sd, grid_y=sd, fanout=m, pct_ring=mix, seed=first_seed + i, sim_ms=sim_ms,
                           name="batch%03d_%dx%d_m%d" % (i, sd, sd, m)))
     return out
+
+
+def serve_request_params(i: int, rng, side=(1, 32), fanouts=(100, 400, 1125), duration=(100, 5000),
+                         first_seed: int = 5000):
+    """One simulation request of the serving workload: grid side log-uniform
+    in [side], fan-out uniform over `fanouts`, duration uniform in [duration]
+    ms; `rng` is a numpy Generator owned by the caller."""
+    import math
+    sd = int(round(math.exp(rng.uniform(math.log(side[0]), math.log(side[1])))))
+    sd = max(side[0], min(side[1], sd))
+    m = int(fanouts[int(rng.integers(0, len(fanouts)))])
+    mix = (40, 30, 20, 10) if sd > 1 else (100, 0, 0, 0)
+    cfg = custom(grid_x=sd, grid_y=sd, fanout=m, pct_ring=mix, seed=first_seed + i,
+                 name="req%04d_%dx%d_m%d" % (i, sd, sd, m))
+    dur = int(rng.integers(duration[0], duration[1] + 1))
+    return cfg, dur
