@@ -54,6 +54,8 @@ extern "C" {
 /* cfg.flags */
 #define SNN_STDP_OFF 1u      /* no depression / potentiation (sd stays 0) */
 #define SNN_DELIVERY_OFF 2u  /* spikes are not delivered (neurons see drive only) */
+#define SNN_FP64 4u          /* physics check: v and u in double precision (same scheme and
+                                operation order; slower neuron update, 8 more bytes per neuron) */
 
 /*
  * Network and model configuration (plain old data).
@@ -82,7 +84,7 @@ typedef struct {
     uint32_t thal_per_col_per_ms;        /* thalamic events per column per ms */
     int32_t thal_amp_q16;                /* current of one thalamic event */
     uint64_t seed;                       /* key of the Philox4x32-10 draws */
-    uint32_t flags;                      /* SNN_STDP_OFF | SNN_DELIVERY_OFF */
+    uint32_t flags;                      /* SNN_STDP_OFF | SNN_DELIVERY_OFF | SNN_FP64 */
     uint32_t reserved;                   /* must be 0 */
     uint64_t raster_capacity;            /* spikes kept on the device; 0 = no raster */
 } snn_config;
@@ -264,6 +266,24 @@ int snn_read_weights(snn_net *net, int32_t *host_w, int32_t *host_sd, size_t cap
 
 /* snn_read_neurons -- v and u of neurons [first, first + count) (host, may be NULL). */
 int snn_read_neurons(snn_net *net, uint32_t first, uint32_t count, float *host_v, float *host_u);
+
+/* snn_read_neurons_f64 -- v and u in double (exact for SNN_FP64 nets, widened otherwise). */
+int snn_read_neurons_f64(snn_net *net, uint32_t first, uint32_t count, double *host_v, double *host_u);
+
+/*
+ * snn_set_probe -- membrane traces of chosen neurons (Sec. 2 "Production of
+ * observables": the trace of the membrane potential and other state
+ * variables of individual neurons can be activated; Fig. 2-3): from the next
+ * step on, v and u of host_gids[0..n) after every step's update are kept on
+ * the device for up to max_steps steps.  n = 0 switches the probe off.
+ * SNN_EINVAL for a gid out of range.
+ */
+int snn_set_probe(snn_net *net, const int32_t *host_gids, uint32_t n, uint32_t max_steps);
+
+/* snn_read_probe -- the traces recorded so far, [step][neuron] order, as
+   float (host buffers of cap values each, either may be NULL);
+   *steps = steps recorded. */
+int snn_read_probe(snn_net *net, float *host_v, float *host_u, size_t cap, uint32_t *steps);
 
 /* snn_read_counters -- event counters and the device error word. */
 int snn_read_counters(snn_net *net, snn_counters *out);

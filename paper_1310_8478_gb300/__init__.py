@@ -7,3 +7,4 @@ from .snn import (  # noqa: F401
     snn_read_raster, snn_read_weights, STDP_OFF, DELIVERY_OFF,
 )
 from .build import build as build_engine  # noqa: F401
+from . import snn  # noqa: F401

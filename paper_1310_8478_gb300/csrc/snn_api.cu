@@ -229,7 +229,7 @@ int check_config(const snn_config *c)
         return SNN_EINVAL;
     }
     if (c->reserved != 0) { set_error("reserved field must be 0"); return SNN_EINVAL; }
-    if (c->flags & ~(SNN_STDP_OFF | SNN_DELIVERY_OFF)) { set_error("unknown flags"); return SNN_EINVAL; }
+    if (c->flags & ~(SNN_STDP_OFF | SNN_DELIVERY_OFF | SNN_FP64)) { set_error("unknown flags"); return SNN_EINVAL; }
     if (c->deriv_period_ms > 0x3fffffffu) { set_error("deriv_period_ms too large"); return SNN_EINVAL; }
     return SNN_OK;
 }
@@ -284,6 +284,7 @@ size_t footprint(const snn_config *c, uint32_t N, int64_t S, int64_t n_rin, bool
     b += ((size_t)N + 1) * 8 * 2;                 // row_off, rin_off
     b += (size_t)n_rin * 12;                      // reverse index + its LTP accumulator
     b += (size_t)N * 24;                          // v u I (hist, last_old) last_spike
+    if (c->flags & SNN_FP64) b += (size_t)N * 16; // v u in double
     b += D * N * 4 + D * 8;                       // ring
     b += (size_t)N * 12 + ((size_t)N / 1024 + 2) * 8;  // build scratch
     if (explicit_net) b += (size_t)S;             // canonical delays
@@ -323,6 +324,10 @@ int alloc_common(snn_net *net)
     SNN_TRY(dalloc_t(net, (size_t)N + 1, &net->rin_off));
     SNN_TRY(dalloc_t(net, (size_t)N, &dn.v));
     SNN_TRY(dalloc_t(net, (size_t)N, &dn.u));
+    if (net->cfg.flags & SNN_FP64) {
+        SNN_TRY(dalloc_t(net, (size_t)N, &dn.vd));
+        SNN_TRY(dalloc_t(net, (size_t)N, &dn.ud));
+    }
     SNN_TRY(dalloc_t(net, (size_t)N, &dn.I));
     SNN_TRY(dalloc_t(net, (size_t)N, &dn.hl));
     SNN_TRY(dalloc_t(net, (size_t)N, &dn.last_spike));
@@ -609,7 +614,9 @@ void launch_step(snn_net *net, int32_t t, cudaStream_t s)
     const int nb_neuron = (int)((net->N + L.neuron_block * kNeuronsPerThread - 1) /
                                 (L.neuron_block * kNeuronsPerThread));
     mark(1);
-    k_neuron<<<nb_neuron, L.neuron_block, 0, s>>>(dn, t_now, t_next);
+    if (dn.vd) k_neuron_f64<<<nb_neuron, L.neuron_block, 0, s>>>(dn, t_now, t_next);
+    else k_neuron_f32<<<nb_neuron, L.neuron_block, 0, s>>>(dn, t_now, t_next);
+    if (dn.probe_n) k_probe<<<(dn.probe_n + 255) / 256, 256, 0, s>>>(dn, t_now);
     mark(1);
 }
 
@@ -1490,8 +1497,88 @@ int snn_read_neurons(snn_net *net, uint32_t first, uint32_t count, float *host_v
 {
     if (!net) { set_error("net is NULL"); return SNN_EINVAL; }
     if ((uint64_t)first + count > net->N) { set_error("neuron range out of bounds"); return SNN_EINVAL; }
+    if (net->dn.vd) {
+        std::vector<double> tmp((size_t)count);
+        const double *src[2] = {net->dn.vd + first, net->dn.ud + first};
+        float *dst[2] = {host_v, host_u};
+        for (int k = 0; k < 2; ++k) {
+            if (!dst[k]) continue;
+            SNN_CUDA(cudaMemcpyAsync(tmp.data(), src[k], (size_t)count * 8, cudaMemcpyDeviceToHost, net->stream));
+            SNN_CUDA(cudaStreamSynchronize(net->stream));
+            for (uint32_t i = 0; i < count; ++i) dst[k][i] = (float)tmp[i];
+        }
+        return SNN_OK;
+    }
     if (host_v) SNN_CUDA(cudaMemcpyAsync(host_v, net->dn.v + first, (size_t)count * 4, cudaMemcpyDeviceToHost, net->stream));
     if (host_u) SNN_CUDA(cudaMemcpyAsync(host_u, net->dn.u + first, (size_t)count * 4, cudaMemcpyDeviceToHost, net->stream));
+    SNN_CUDA(cudaStreamSynchronize(net->stream));
+    return SNN_OK;
+}
+
+int snn_read_neurons_f64(snn_net *net, uint32_t first, uint32_t count, double *host_v, double *host_u)
+{
+    if (!net) { set_error("net is NULL"); return SNN_EINVAL; }
+    if ((uint64_t)first + count > net->N) { set_error("neuron range out of bounds"); return SNN_EINVAL; }
+    if (net->dn.vd) {
+        if (host_v) SNN_CUDA(cudaMemcpyAsync(host_v, net->dn.vd + first, (size_t)count * 8, cudaMemcpyDeviceToHost, net->stream));
+        if (host_u) SNN_CUDA(cudaMemcpyAsync(host_u, net->dn.ud + first, (size_t)count * 8, cudaMemcpyDeviceToHost, net->stream));
+        SNN_CUDA(cudaStreamSynchronize(net->stream));
+        return SNN_OK;
+    }
+    std::vector<float> tmp((size_t)count);
+    const float *src[2] = {net->dn.v + first, net->dn.u + first};
+    double *dst[2] = {host_v, host_u};
+    for (int k = 0; k < 2; ++k) {
+        if (!dst[k]) continue;
+        SNN_CUDA(cudaMemcpyAsync(tmp.data(), src[k], (size_t)count * 4, cudaMemcpyDeviceToHost, net->stream));
+        SNN_CUDA(cudaStreamSynchronize(net->stream));
+        for (uint32_t i = 0; i < count; ++i) dst[k][i] = tmp[i];
+    }
+    return SNN_OK;
+}
+
+int snn_set_probe(snn_net *net, const int32_t *host_gids, uint32_t n, uint32_t max_steps)
+{
+    if (!net) { set_error("net is NULL"); return SNN_EINVAL; }
+    DevNet &dn = net->dn;
+    dfree(net, (void *)dn.probe_gid);
+    dfree(net, dn.probe_v);
+    dfree(net, dn.probe_u);
+    dn.probe_gid = nullptr;
+    dn.probe_v = dn.probe_u = nullptr;
+    dn.probe_n = dn.probe_cap = 0;
+    drop_graphs(net);
+    if (n == 0 || max_steps == 0) return SNN_OK;
+    if (!host_gids) { set_error("gids are NULL"); return SNN_EINVAL; }
+    for (uint32_t k = 0; k < n; ++k)
+        if (host_gids[k] < 0 || (uint32_t)host_gids[k] >= net->N) { set_error("probe gid %d out of range", host_gids[k]); return SNN_EINVAL; }
+    int32_t *g = nullptr;
+    float *pv = nullptr, *pu = nullptr;
+    SNN_TRY(dalloc_t(net, n, &g));
+    SNN_TRY(dalloc_t(net, (size_t)n * max_steps, &pv));
+    SNN_TRY(dalloc_t(net, (size_t)n * max_steps, &pu));
+    SNN_CUDA(cudaMemcpyAsync(g, host_gids, (size_t)n * 4, cudaMemcpyHostToDevice, net->stream));
+    SNN_CUDA(cudaStreamSynchronize(net->stream));
+    dn.probe_gid = g;
+    dn.probe_v = pv;
+    dn.probe_u = pu;
+    dn.probe_n = n;
+    dn.probe_cap = max_steps;
+    dn.probe_t0 = net->t;
+    return SNN_OK;
+}
+
+int snn_read_probe(snn_net *net, float *host_v, float *host_u, size_t cap, uint32_t *steps)
+{
+    if (!net) { set_error("net is NULL"); return SNN_EINVAL; }
+    const DevNet &dn = net->dn;
+    const uint32_t rec = dn.probe_n ? (uint32_t)std::min<int64_t>(dn.probe_cap, std::max(0, net->t - dn.probe_t0)) : 0;
+    if (steps) *steps = rec;
+    const size_t need = (size_t)rec * dn.probe_n;
+    if (need > cap && (host_v || host_u)) { set_error("need %zu values", need); return SNN_ETRUNC; }
+    if (need == 0) return SNN_OK;
+    if (host_v) SNN_CUDA(cudaMemcpyAsync(host_v, dn.probe_v, need * 4, cudaMemcpyDeviceToHost, net->stream));
+    if (host_u) SNN_CUDA(cudaMemcpyAsync(host_u, dn.probe_u, need * 4, cudaMemcpyDeviceToHost, net->stream));
     SNN_CUDA(cudaStreamSynchronize(net->stream));
     return SNN_OK;
 }
@@ -1561,7 +1648,8 @@ int snn_save_state(snn_net *net, void *host_buf, size_t cap, size_t *n)
 {
     if (!net || !n) { set_error("NULL argument"); return SNN_EINVAL; }
     const size_t N = net->N, D = net->cfg.max_delay_ms, S = (size_t)net->S_store;
-    const size_t need = sizeof(StateHeader) + N * 24 + D * N * 4 + D * 8 + S * 8 + sizeof(DevCounters);
+    const size_t fsz = net->dn.vd ? 8 : 4;      // v and u in double for SNN_FP64 nets
+    const size_t need = sizeof(StateHeader) + N * (16 + 2 * fsz) + D * N * 4 + D * 8 + S * 8 + sizeof(DevCounters);
     *n = need;
     if (!host_buf) return SNN_OK;
     SNN_TRY(flush_owed(net));
@@ -1580,8 +1668,10 @@ int snn_save_state(snn_net *net, void *host_buf, size_t cap, size_t *n)
     p += sizeof h;
     cudaStream_t s = net->stream;
     const DevNet &dn = net->dn;
-    const void *src[] = {dn.v, dn.u, dn.I, dn.hl, dn.last_spike, dn.ring_ids, dn.ring_cnt, net->w, net->sd, net->ctr};
-    const size_t len[] = {N * 4, N * 4, N * 4, N * 8, N * 4, D * N * 4, D * 8, S * 4, S * 4, sizeof(DevCounters)};
+    const void *sv = dn.vd ? (const void *)dn.vd : (const void *)dn.v;
+    const void *su = dn.ud ? (const void *)dn.ud : (const void *)dn.u;
+    const void *src[] = {sv, su, dn.I, dn.hl, dn.last_spike, dn.ring_ids, dn.ring_cnt, net->w, net->sd, net->ctr};
+    const size_t len[] = {N * fsz, N * fsz, N * 4, N * 8, N * 4, D * N * 4, D * 8, S * 4, S * 4, sizeof(DevCounters)};
     for (int k = 0; k < 10; ++k) {
         if (len[k]) SNN_CUDA(cudaMemcpyAsync(p, src[k], len[k], cudaMemcpyDeviceToHost, s));
         p += len[k];
@@ -1594,7 +1684,8 @@ int snn_load_state(snn_net *net, const void *host_buf, size_t n)
 {
     if (!net || !host_buf) { set_error("NULL argument"); return SNN_EINVAL; }
     const size_t N = net->N, D = net->cfg.max_delay_ms, S = (size_t)net->S_store;
-    const size_t need = sizeof(StateHeader) + N * 24 + D * N * 4 + D * 8 + S * 8 + sizeof(DevCounters);
+    const size_t fsz = net->dn.vd ? 8 : 4;
+    const size_t need = sizeof(StateHeader) + N * (16 + 2 * fsz) + D * N * 4 + D * 8 + S * 8 + sizeof(DevCounters);
     if (n < need) { set_error("checkpoint is %zu bytes, need %zu", n, need); return SNN_EINVAL; }
     StateHeader h{};
     std::memcpy(&h, host_buf, sizeof h);
@@ -1606,8 +1697,10 @@ int snn_load_state(snn_net *net, const void *host_buf, size_t n)
     const char *p = (const char *)host_buf + sizeof h;
     cudaStream_t s = net->stream;
     DevNet &dn = net->dn;
-    void *dst[] = {dn.v, dn.u, dn.I, dn.hl, dn.last_spike, dn.ring_ids, dn.ring_cnt, net->w, net->sd, net->ctr};
-    const size_t len[] = {N * 4, N * 4, N * 4, N * 8, N * 4, D * N * 4, D * 8, S * 4, S * 4, sizeof(DevCounters)};
+    void *sv = dn.vd ? (void *)dn.vd : (void *)dn.v;
+    void *su = dn.ud ? (void *)dn.ud : (void *)dn.u;
+    void *dst[] = {sv, su, dn.I, dn.hl, dn.last_spike, dn.ring_ids, dn.ring_cnt, net->w, net->sd, net->ctr};
+    const size_t len[] = {N * fsz, N * fsz, N * 4, N * 8, N * 4, D * N * 4, D * 8, S * 4, S * 4, sizeof(DevCounters)};
     for (int k = 0; k < 10; ++k) {
         if (len[k]) SNN_CUDA(cudaMemcpyAsync(dst[k], p, len[k], cudaMemcpyHostToDevice, s));
         p += len[k];

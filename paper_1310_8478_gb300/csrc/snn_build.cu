@@ -231,6 +231,10 @@ __global__ void k_init_state(DevNet n)
         const float v0 = -65.0f;
         n.v[i] = v0;
         n.u[i] = __fmul_rn(0.2f, v0);
+        if (n.vd) {
+            n.vd[i] = -65.0;
+            n.ud[i] = __dmul_rn(0.2, -65.0);
+        }
         n.I[i] = 0;
         n.hl[i] = make_uint2(0u, (uint32_t)kNever);
         n.last_spike[i] = kNever;

@@ -57,6 +57,11 @@ struct DevNet {
                                      //         and every read
     int64_t n_rin;
     float *v, *u;                    // [N] membrane potential, recovery variable
+    double *vd, *ud;                 // [N] the same in double (SNN_FP64 nets), else NULL
+    const int32_t *probe_gid;        // [probe_n] neurons whose v, u are traced
+    float *probe_v, *probe_u;        // [probe_cap][probe_n]
+    uint32_t probe_n, probe_cap;
+    int32_t probe_t0;                // step stored in row 0
     int32_t *I;                      // [N] Q16 input accumulated during S1/S2
     uint2 *hl;                       // [N] x: bit k = fired at step t - k; y: latest spike
                                      //     older than that 32-step window (one 8-byte word,
@@ -252,7 +257,9 @@ __global__ void k_read_rows(DevNet n, GenParams g, const uint8_t *canon_delay, u
 
 __global__ void k_deliver(DevNet n, const int *t_now);
 __global__ void k_dense(DevNet n, const int *t_now);
-__global__ void k_neuron(DevNet n, const int *t_now, int *t_next);
+__global__ void k_neuron_f32(DevNet n, const int *t_now, int *t_next);
+__global__ void k_neuron_f64(DevNet n, const int *t_now, int *t_next);
+__global__ void k_probe(DevNet n, const int *t_now);
 __global__ void k_ltp(DevNet n, const int *t_now, int force);
 __global__ void k_deriv(DevNet n, const int *t_now, int force);
 __global__ void k_fold(DevNet n, const int *t_now, int force);

@@ -559,8 +559,50 @@ __device__ __forceinline__ bool izhikevich_step(float &v, float &u, int32_t iq, 
     return false;
 }
 
-__global__ void __launch_bounds__(1024) k_neuron(DevNet n, const int *t_now, int *t_next)
+// the same scheme in double (SNN_FP64): identical operation order, decimal
+// parameters
+__device__ __forceinline__ bool izhikevich_step(double &v, double &u, int32_t iq, bool exc)
 {
+    const double a = exc ? 0.02 : 0.1;
+    const double b = 0.2;
+    const double c = -65.0;
+    const double d = exc ? 8.0 : 2.0;
+    const double cur = __dmul_rn(__int2double_rn(iq), 0x1p-16);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        double x = __dmul_rn(0.04, v);
+        x = __dadd_rn(x, 5.0);
+        x = __dmul_rn(x, v);
+        x = __dadd_rn(x, 140.0);
+        x = __dsub_rn(x, u);
+        x = __dadd_rn(x, cur);
+        x = __dmul_rn(0.5, x);
+        v = __dadd_rn(v, x);
+    }
+    double y = __dmul_rn(b, v);
+    y = __dsub_rn(y, u);
+    y = __dmul_rn(a, y);
+    u = __dadd_rn(u, y);
+    if (v >= 30.0) {
+        v = c;
+        u = __dadd_rn(u, d);
+        return true;
+    }
+    return false;
+}
+
+template <typename F> __device__ __forceinline__ F *state_v(const DevNet &n);
+template <> __device__ __forceinline__ float *state_v<float>(const DevNet &n) { return n.v; }
+template <> __device__ __forceinline__ double *state_v<double>(const DevNet &n) { return n.vd; }
+template <typename F> __device__ __forceinline__ F *state_u(const DevNet &n);
+template <> __device__ __forceinline__ float *state_u<float>(const DevNet &n) { return n.u; }
+template <> __device__ __forceinline__ double *state_u<double>(const DevNet &n) { return n.ud; }
+
+template <typename F>
+__device__ __forceinline__ void neuron_body(const DevNet &n, const int *t_now, int *t_next)
+{
+    F *const sv = state_v<F>(n);
+    F *const su = state_u<F>(n);
     const int t = *t_now;
     const int par = t & 1;
     const uint32_t tile = blockDim.x * kNeuronsPerThread;
@@ -569,15 +611,15 @@ __global__ void __launch_bounds__(1024) k_neuron(DevNet n, const int *t_now, int
     unsigned long long indeg = 0;     // excitatory in-degree of the neurons that fired
     // all loads of the thread's neurons first, then the updates and stores
     int32_t iq[kNeuronsPerThread];
-    float vv[kNeuronsPerThread], uu[kNeuronsPerThread];
+    F vv[kNeuronsPerThread], uu[kNeuronsPerThread];
     uint2 hh[kNeuronsPerThread];
 #pragma unroll
     for (int it = 0; it < kNeuronsPerThread; ++it) {
         const uint32_t i = first + it * blockDim.x + threadIdx.x;
         if (i < n.N) {
             iq[it] = n.I[i];
-            vv[it] = n.v[i];
-            uu[it] = n.u[i];
+            vv[it] = sv[i];
+            uu[it] = su[i];
             hh[it] = n.hl[i];
         }
     }
@@ -586,11 +628,11 @@ __global__ void __launch_bounds__(1024) k_neuron(DevNet n, const int *t_now, int
         const uint32_t i = first + it * blockDim.x + threadIdx.x;
         if (i >= n.N) break;
         const bool exc = (i % n.npc) < n.ne;
-        float v = vv[it], u = uu[it];
+        F v = vv[it], u = uu[it];
         const bool fired = izhikevich_step(v, u, iq[it], exc);
         n.I[i] = 0;
-        n.v[i] = v;
-        n.u[i] = u;
+        sv[i] = v;
+        su[i] = u;
         uint2 h = hh[it];
         if (h.x & 0x80000000u) h.y = (uint32_t)(t - 32);
         h.x = (h.x << 1) | (fired ? 1u : 0u);
@@ -683,6 +725,33 @@ __global__ void __launch_bounds__(1024) k_neuron(DevNet n, const int *t_now, int
     c->ltp_pending = t;
     c->done_blocks = 0;
     *t_next = t + 1;
+}
+
+}  // namespace snn
+
+namespace snn {
+
+__global__ void __launch_bounds__(1024) k_neuron_f32(DevNet n, const int *t_now, int *t_next)
+{
+    neuron_body<float>(n, t_now, t_next);
+}
+
+__global__ void __launch_bounds__(1024) k_neuron_f64(DevNet n, const int *t_now, int *t_next)
+{
+    neuron_body<double>(n, t_now, t_next);
+}
+
+// membrane traces: v and u of the probed neurons after the update of step t
+__global__ void k_probe(DevNet n, const int *t_now)
+{
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n.probe_n) return;
+    const int row = *t_now - n.probe_t0;
+    if (row < 0 || (uint32_t)row >= n.probe_cap) return;
+    const int32_t g = n.probe_gid[k];
+    const size_t o = (size_t)row * n.probe_n + k;
+    n.probe_v[o] = n.vd ? (float)n.vd[g] : n.v[g];
+    n.probe_u[o] = n.ud ? (float)n.ud[g] : n.u[g];
 }
 
 }  // namespace snn

@@ -19,6 +19,7 @@ from . import build as _build
 # ---------------------------------------------------------------------------
 STDP_OFF = 1
 DELIVERY_OFF = 2
+FP64 = 4
 
 OK, EINVAL, ENOMEM, ECUDA, EOVERFLOW, ETIMEOUT, ETRUNC, ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
 SNN_NOALLOC_MAX_SYNAPSES = 1 << 20   # staging size of snn_read_synapses_noalloc
@@ -104,6 +105,9 @@ _SIGS = {
     "snn_read_weights": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_size_t, _P(ctypes.c_size_t)]),
     "snn_read_neurons": (ctypes.c_int, [_vp, ctypes.c_uint32, ctypes.c_uint32, _vp, _vp]),
     "snn_read_counters": (ctypes.c_int, [_vp, _P(SnnCounters)]),
+    "snn_read_neurons_f64": (ctypes.c_int, [_vp, ctypes.c_uint32, ctypes.c_uint32, _vp, _vp]),
+    "snn_set_probe": (ctypes.c_int, [_vp, _vp, ctypes.c_uint32, ctypes.c_uint32]),
+    "snn_read_probe": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_size_t, _P(ctypes.c_uint32)]),
     "snn_net_info": (ctypes.c_int, [_vp, _P(ctypes.c_uint32), _P(ctypes.c_int64), _P(ctypes.c_size_t)]),
     "snn_set_profile": (ctypes.c_int, [_vp, ctypes.c_int]),
     "snn_read_profile": (ctypes.c_int, [_vp, _P(SnnProfile)]),
@@ -403,6 +407,30 @@ class Network:
         u = np.empty(max(count, 1), np.float32)
         _check(self._lib.snn_read_neurons(self.h, first, count, _ptr(v), _ptr(u)), "snn_read_neurons")
         return dict(v=v[:count], u=u[:count])
+
+    def neurons_f64(self, first: int = 0, count: int | None = None):
+        count = self.n_neurons - first if count is None else count
+        v = np.empty(max(count, 1), np.float64)
+        u = np.empty(max(count, 1), np.float64)
+        _check(self._lib.snn_read_neurons_f64(self.h, first, count, _ptr(v), _ptr(u)), "snn_read_neurons_f64")
+        return dict(v=v[:count], u=u[:count])
+
+    def set_probe(self, gids, max_steps: int):
+        g = np.ascontiguousarray(gids, np.int32)
+        _check(self._lib.snn_set_probe(self.h, _ptr(g) if len(g) else None, len(g), int(max_steps)), "snn_set_probe")
+        self._probe_n = len(g)
+
+    def probe(self):
+        """(v, u) traces recorded so far, arrays of shape (steps, probed neurons)."""
+        steps = ctypes.c_uint32(0)
+        _check(self._lib.snn_read_probe(self.h, None, None, 0, ctypes.byref(steps)), "snn_read_probe")
+        k = getattr(self, "_probe_n", 0)
+        v = np.empty(max(steps.value * k, 1), np.float32)
+        u = np.empty(max(steps.value * k, 1), np.float32)
+        _check(self._lib.snn_read_probe(self.h, _ptr(v), _ptr(u), steps.value * k, ctypes.byref(steps)),
+               "snn_read_probe")
+        n = steps.value * k
+        return v[:n].reshape(steps.value, k), u[:n].reshape(steps.value, k)
 
     def counters(self) -> dict:
         c = SnnCounters()
