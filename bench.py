@@ -425,7 +425,7 @@ def main():
     rate_hz = d_spikes / n_neurons / (K / 1000.0)
     n_exc_syn = cfg["grid_x"] * cfg["grid_y"] * cfg["exc_per_col"] * cfg["fanout"]
     # algorithmic bytes moved by each kernel over the timed region (the
-    # per-unit figures are in the design doc): 8 B per delivered event (target +
+    # per-unit figures): 8 B per delivered event (target +
     # weight), 8 B per event on a plastic synapse (sd read + write), 12 B per
     # potentiation visit, 16 B per plastic synapse per long-term update,
     # 32 B per neuron per step
