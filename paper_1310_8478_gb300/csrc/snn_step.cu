@@ -322,6 +322,111 @@ size_t dense_smem_bytes(uint32_t npc, uint32_t block)
            + (((size_t)kSlots * npc + 15) & ~size_t(15));  // lags (bytes)
 }
 
+// One row of the dense pass: the lane takes 8 consecutive synapses per pass,
+// with one 16-byte target load and two 16-byte weight and derivative loads;
+// the delay bucket of each synapse (its deliver flag and LTP amount) is
+// tracked in registers.  kDeriv: the step closes a plasticity period (the
+// long-term update runs between LTP and delivery).
+template <bool kDeriv>
+__device__ __forceinline__ unsigned long long dense_row_walk(const DevNet &n, int64_t base, int m, int D, bool exc,
+                                                             bool stdp, bool ltp_on, uint32_t npc,
+                                                             const int32_t *w_off, const uint32_t *w_flag,
+                                                             const int32_t *w_amt, int32_t *s_in,
+                                                             const uint8_t *s_lag, const int32_t *s_lutm, int lane)
+{
+    const uint4 *rt4 = reinterpret_cast<const uint4 *>(n.tgt16 + base);
+    int4 *rw4 = reinterpret_cast<int4 *>(n.w + base);
+    int4 *rs4 = reinterpret_cast<int4 *>(n.sd + base);
+    const bool all_deriv = kDeriv && exc;
+    unsigned visits = 0;
+    for (int c = lane; c * 8 < m; c += 32) {
+        const int k0 = c * 8;
+        int lo = 1, hi = D;                   // bucket of k0: first d with end > k0
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (w_off[mid] > k0) hi = mid; else lo = mid + 1;
+        }
+        // the current bucket's end, flag and amount stay in registers; a
+        // synapse past the end (rare) moves to the next non-empty bucket
+        int d = lo;
+        int nb = w_off[d];
+        bool fcur = w_flag[d] != 0;
+        int32_t acur = exc ? w_amt[d] : 0;
+        uint32_t vmask = 0, fmask = 0;
+        int32_t am[8];
+        bool any_f = false, any_a = false;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int k = k0 + u;
+            const bool valid = k < m;
+            if (valid && k >= nb) {
+                do {
+                    ++d;
+                } while (k >= w_off[d]);
+                nb = w_off[d];
+                fcur = w_flag[d] != 0;
+                acur = exc ? w_amt[d] : 0;
+            }
+            vmask |= (valid ? 1u : 0u) << u;
+            fmask |= (valid && fcur ? 1u : 0u) << u;
+            am[u] = valid ? acur : 0;
+            any_f |= valid && fcur;
+            any_a |= am[u] != 0;
+        }
+        const bool need_w = all_deriv || any_f;
+        const bool need_sd = all_deriv || (exc && stdp && any_f) || any_a;
+        if (!need_w && !need_sd) continue;
+        const uint4 tv = rt4[c];
+        int4 wa = make_int4(0, 0, 0, 0), wb = wa, sa = wa, sb = wa;
+        if (need_w) {
+            wa = rw4[2 * c];
+            wb = rw4[2 * c + 1];
+        }
+        if (need_sd) {
+            sa = rs4[2 * c];
+            sb = rs4[2 * c + 1];
+        }
+        const uint32_t tw[4] = {tv.x, tv.y, tv.z, tv.w};
+        int32_t wv[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+        int32_t sv[8] = {sa.x, sa.y, sa.z, sa.w, sb.x, sb.y, sb.z, sb.w};
+        bool sd_dirty = false;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const bool f = (fmask >> u) & 1u;
+            if (!((vmask >> u) & 1u) || !(f || am[u] || all_deriv)) continue;
+            const uint32_t v = (u & 1) ? (tw[u >> 1] >> 16) : (tw[u >> 1] & 0xffffu);
+            const uint32_t idx = (v >> 12) * npc + (v & 0xfffu);
+            if (!exc) {
+                atomicAdd(&s_in[idx], wv[u]);
+                continue;
+            }
+            const int lag = s_lag[idx];
+            const bool pot = am[u] && lag == 1;
+            const int32_t dep = (f && stdp) ? s_lutm[lag] : 0;
+            if (ltp_on && lag == 1) visits++;
+            int32_t sdv = sv[u];
+            if (pot) sdv += am[u];
+            if (kDeriv) {
+                wv[u] = deriv_w(n, wv[u], sdv);
+                sdv = deriv_sd(n, sdv);
+            }
+            if (f) atomicAdd(&s_in[idx], wv[u]);
+            sdv -= dep;
+            sd_dirty |= pot || kDeriv || dep;
+            sv[u] = sdv;
+        }
+        if (sd_dirty) {
+            rs4[2 * c] = make_int4(sv[0], sv[1], sv[2], sv[3]);
+            rs4[2 * c + 1] = make_int4(sv[4], sv[5], sv[6], sv[7]);
+        }
+        if (all_deriv) {
+            rw4[2 * c] = make_int4(wv[0], wv[1], wv[2], wv[3]);
+            rw4[2 * c + 1] = make_int4(wv[4], wv[5], wv[6], wv[7]);
+        }
+    }
+    return visits;
+}
+
 __global__ void __launch_bounds__(512) k_dense(DevNet n, const int *t_now)
 {
     extern __shared__ int4 smem_i4[];
@@ -408,88 +513,12 @@ __global__ void __launch_bounds__(512) k_dense(DevNet n, const int *t_now)
         if (busy) {
             const int m = off[D];
             const int64_t base = row_base(n, p);     // a multiple of 8: rows are padded
-            const uint4 *rt4 = reinterpret_cast<const uint4 *>(n.tgt16 + base);
-            int4 *rw4 = reinterpret_cast<int4 *>(n.w + base);
-            int4 *rs4 = reinterpret_cast<int4 *>(n.sd + base);
-            const bool all_deriv = exc && deriv_on;
-            // lane takes 8 consecutive synapses per pass: one 16-byte load of
-            // targets, two of weights, two of derivatives
-            for (int c = lane; c * 8 < m; c += 32) {
-                const int k0 = c * 8;
-                int lo = 1, hi = D;                   // bucket of k0: first d with end > k0
-                while (lo < hi) {
-                    const int mid = (lo + hi) >> 1;
-                    if (w_off[mid] > k0) hi = mid; else lo = mid + 1;
-                }
-                int d = lo;
-                uint32_t vmask = 0, fmask = 0;
-                int32_t am[8];
-                bool need_w = all_deriv, need_sd = all_deriv;
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    am[u] = 0;
-                    const int k = k0 + u;
-                    if (k < m) {
-                        while (k >= w_off[d]) ++d;
-                        vmask |= 1u << u;
-                        if (w_flag[d]) {
-                            fmask |= 1u << u;
-                            need_w = true;
-                            need_sd |= exc && stdp;
-                        }
-                        if (exc) am[u] = w_amt[d];
-                        need_sd |= am[u] != 0;
-                    }
-                }
-                if (!need_w && !need_sd) continue;
-                const uint4 tv = rt4[c];
-                int4 wa = make_int4(0, 0, 0, 0), wb = wa, sa = wa, sb = wa;
-                if (need_w) {
-                    wa = rw4[2 * c];
-                    wb = rw4[2 * c + 1];
-                }
-                if (need_sd) {
-                    sa = rs4[2 * c];
-                    sb = rs4[2 * c + 1];
-                }
-                const uint32_t tw[4] = {tv.x, tv.y, tv.z, tv.w};
-                int32_t wv[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
-                int32_t sv[8] = {sa.x, sa.y, sa.z, sa.w, sb.x, sb.y, sb.z, sb.w};
-                bool sd_dirty = false;
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const bool f = (fmask >> u) & 1u;
-                    if (!((vmask >> u) & 1u) || !(f || am[u] || all_deriv)) continue;
-                    const uint32_t v = (u & 1) ? (tw[u >> 1] >> 16) : (tw[u >> 1] & 0xffffu);
-                    const uint32_t idx = (v >> 12) * npc + (v & 0xfffu);
-                    if (!exc) {
-                        atomicAdd(&s_in[idx], wv[u]);
-                        continue;
-                    }
-                    const int lag = s_lag[idx];
-                    const bool pot = am[u] && lag == 1;
-                    const int32_t dep = (f && stdp) ? s_lutm[lag] : 0;
-                    if (ltp_on && lag == 1) visits++;
-                    int32_t sdv = sv[u];
-                    if (pot) sdv += am[u];
-                    if (deriv_on) {
-                        wv[u] = deriv_w(n, wv[u], sdv);
-                        sdv = deriv_sd(n, sdv);
-                    }
-                    if (f) atomicAdd(&s_in[idx], wv[u]);
-                    sdv -= dep;
-                    sd_dirty |= pot || deriv_on || dep;
-                    sv[u] = sdv;
-                }
-                if (sd_dirty) {
-                    rs4[2 * c] = make_int4(sv[0], sv[1], sv[2], sv[3]);
-                    rs4[2 * c + 1] = make_int4(sv[4], sv[5], sv[6], sv[7]);
-                }
-                if (all_deriv) {
-                    rw4[2 * c] = make_int4(wv[0], wv[1], wv[2], wv[3]);
-                    rw4[2 * c + 1] = make_int4(wv[4], wv[5], wv[6], wv[7]);
-                }
-            }
+            if (deriv_on)
+                visits += dense_row_walk<true>(n, base, m, D, exc, stdp, ltp_on, npc, w_off, w_flag, w_amt, s_in,
+                                               s_lag, s_lutm, lane);
+            else
+                visits += dense_row_walk<false>(n, base, m, D, exc, stdp, ltp_on, npc, w_off, w_flag, w_amt, s_in,
+                                                s_lag, s_lutm, lane);
         }
         __syncwarp();
     }
