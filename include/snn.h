@@ -119,7 +119,7 @@ typedef struct {
     uint32_t ltp_blocks_per_sm;
     uint32_t deriv_block;
     uint32_t graph_steps;            /* steps per captured CUDA graph; even; 1 = no graphs */
-    uint32_t dense_block;            /* threads per block of the dense synapse pass (32..512) */
+    uint32_t dense_block;            /* threads per block of the dense synapse pass (32..1024) */
     uint32_t dense_rows;             /* source rows per block of the dense pass */
     uint32_t dense_permille;         /* a step takes the dense pass when at least this many
                                         neurons per 1000 fired in the step before; 1001 = never */
@@ -374,7 +374,10 @@ const char *snn_last_error(void);
 /*
  * snn_set_allocator -- route device allocations of nets built afterwards
  * through alloc(bytes, stream, ctx) / release(ptr, ctx) (e.g. a framework's
- * caching allocator).  NULL restores cudaMalloc / cudaFree.
+ * caching allocator).  NULL restores cudaMalloc / cudaFree.  Blocks must be
+ * 256-byte aligned (the kernels use 16-byte vector accesses and bulk L2
+ * prefetches); a misaligned block is released and the build fails with
+ * SNN_ENOMEM.
  */
 void snn_set_allocator(void *(*alloc)(size_t bytes, void *stream, void *ctx),
                        void (*release)(void *ptr, void *ctx), void *ctx);

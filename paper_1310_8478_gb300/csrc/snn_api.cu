@@ -157,6 +157,11 @@ int dalloc(snn_net *net, size_t bytes, void **out)
             set_error("allocator hook failed for %zu bytes", bytes);
             return SNN_ENOMEM;
         }
+        if ((uintptr_t)p & 255u) {
+            if (net->release) net->release(p, net->alloc_ctx);
+            set_error("allocator hook returned a block that is not 256-byte aligned");
+            return SNN_ENOMEM;
+        }
     } else {
         cudaError_t e = cudaMalloc(&p, bytes);
         if (e != cudaSuccess) {
@@ -351,6 +356,7 @@ int alloc_common(snn_net *net)
     dn.doff = net->doff;
     dn.tgt = net->tgt;
     dn.tgt16 = net->tgt16;
+    dn.npc_recip = (uint32_t)(((1ull << 31) + net->cfg.neurons_per_col - 1) / net->cfg.neurons_per_col);
     dn.nbr = net->nbr;
     dn.w = net->w;
     dn.sd = net->sd;
@@ -380,6 +386,11 @@ int setup_dense(snn_net *net)
 {
     net->dense_ok = false;
     if (!net->tgt16 || net->cfg.neurons_per_col > kDenseMaxNpc) return SNN_OK;
+    // the dense pass packs each depression amount into 15 bits
+    std::vector<int32_t> lut;
+    if (build_luts(&net->cfg, lut) != SNN_OK) return SNN_OK;
+    for (int k = 0; k < kLut; ++k)
+        if (lut[kLut + k] < 0 || lut[kLut + k] > 0x7fff) return SNN_OK;
     const size_t bytes = dense_smem_bytes(net->cfg.neurons_per_col, net->launch.dense_block);
     int optin = 0;
     SNN_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, net->device));
@@ -388,12 +399,12 @@ int setup_dense(snn_net *net)
     int per_sm = 0;
     SNN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dense, (int)net->launch.dense_block, bytes));
     if (per_sm < 1) return SNN_OK;
-    // rows per block: the launch's value, or (0) enough blocks for about 16
+    // rows per block: the launch's value, or (0) enough blocks for about 8
     // waves of resident blocks, with at least 64 rows to pay for the staging
     uint32_t rows = net->launch.dense_rows;
     if (rows == 0) {
         const uint32_t npc = net->cfg.neurons_per_col, C = net->dn.C;
-        const uint64_t want = 16ull * per_sm * net->sm_count;
+        const uint64_t want = 8ull * per_sm * net->sm_count;
         uint32_t chunks = (uint32_t)std::max<uint64_t>(1, (want + C - 1) / C);
         chunks = std::min(chunks, std::max(1u, npc / 64));
         rows = (npc + chunks - 1) / chunks;
@@ -1060,8 +1071,8 @@ int snn_set_launch(snn_net *net, const snn_launch *launch)
     for (uint32_t b : {L.deliver_block, L.neuron_block, L.ltp_block, L.deriv_block}) {
         if (b < 32 || b > 1024 || b % 32) { set_error("block sizes must be multiples of 32 in 32..1024"); return SNN_EINVAL; }
     }
-    if (L.dense_block < 32 || L.dense_block > 512 || L.dense_block % 32) {
-        set_error("dense_block must be a multiple of 32 in 32..512");
+    if (L.dense_block < 32 || L.dense_block > 1024 || L.dense_block % 32) {
+        set_error("dense_block must be a multiple of 32 in 32..1024");
         return SNN_EINVAL;
     }
     if (L.deliver_blocks_per_sm > 64 || L.ltp_blocks_per_sm > 64) { set_error("blocks per SM must be <= 64"); return SNN_EINVAL; }

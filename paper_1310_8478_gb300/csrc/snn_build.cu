@@ -64,7 +64,7 @@ __global__ void k_gen_rows(GenParams g, uint32_t n_rows, uint16_t *doff, int32_t
             if (active && rank == __popc(peers) - 1) s_cur[warp][d] = start + __popc(peers);
             if (active) {
                 const int64_t pos = base + start + rank;
-                if (tgt16) tgt16[pos] = (uint16_t)((sl << 12) | (t % g.npc));
+                if (tgt16) tgt16[pos] = (uint16_t)(sl * g.npc + t % g.npc);
                 else tgt[pos] = (int32_t)t;
                 w[pos] = exc ? g.w_exc0 : g.w_inh0;
                 sd[pos] = 0;

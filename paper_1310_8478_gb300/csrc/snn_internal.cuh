@@ -17,8 +17,9 @@ constexpr int kKinds = 5;            // profiled kernel kinds: deliver, neuron, 
 constexpr int kSlots = 13;           // own column + 3 rings of 4 neighbour columns
 constexpr int kSlotStride = 16;      // entries per column in the neighbour table
 constexpr int32_t kNoPending = -(1 << 30);  // ltp_pending value when no LTP is owed
-constexpr uint32_t kMaxCompactNpc = 4096;    // 12-bit local ids in the compact target format
-constexpr uint32_t kDenseMaxNpc = 3200;      // staged columns must fit in shared memory
+constexpr uint32_t kMaxCompactNpc = 4096;    // compact targets slot * npc + local stay below 2^16
+constexpr uint32_t kDenseMaxNpc = 2800;      // staged columns must fit in shared memory
+static_assert(kSlots * kMaxCompactNpc <= 65536, "compact targets must fit 16 bits");
 constexpr int kUnroll = 4;                   // dense pass: positions per lane in flight
 
 // Device counters and per-step bookkeeping (one struct, device memory).
@@ -33,6 +34,8 @@ struct DevCounters {
     unsigned done_blocks;            // blocks of k_neuron finished (last block closes the step)
     unsigned long long dense_e_all, dense_e_exc, dense_l_exc;  // work done by the dense pass
     unsigned long long dense_steps, dense_deriv_steps;
+    unsigned long long l_exc_mark;   // l_exc when the last step closed
+    unsigned long long l_exc_last;   // excitatory in-degree of the neurons that fired in the last step
 };
 
 // Everything a step kernel needs, passed by value.
@@ -46,7 +49,8 @@ struct DevNet {
     const int64_t *row_off;          // [N + 1] first synapse of every source row
     const uint16_t *doff;            // [N][kDoffStride]: synapses of delay <= d, d = 0..D
     int32_t *tgt;                    // [S] target gid (explicit nets / big columns), or NULL
-    uint16_t *tgt16;                 // [S] compact target: slot << 12 | local id, or NULL
+    uint16_t *tgt16;                 // [S] compact target: slot * npc + local id, or NULL
+    uint32_t npc_recip;              // ceil(2^31 / npc): slot = (v * npc_recip) >> 31 for v < 2^16
     const int32_t *nbr;              // [C][kSlotStride] global column of every slot
     int32_t *w, *sd;                 // [S] weight, STDP derivative; rows sorted by delay
     const int64_t *rin_off;          // [N + 1] reverse index (incoming excitatory synapses)
@@ -204,7 +208,8 @@ __device__ __forceinline__ uint32_t target_gid(const DevNet &n, uint32_t src_col
 {
     if (n.tgt16) {
         const uint32_t v = n.tgt16[k];
-        return (uint32_t)n.nbr[src_col * kSlotStride + (v >> 12)] * n.npc + (v & 0xfffu);
+        const uint32_t slot = (uint32_t)(((uint64_t)v * n.npc_recip) >> 31);
+        return (uint32_t)n.nbr[src_col * kSlotStride + slot] * n.npc + (v - slot * n.npc);
     }
     return (uint32_t)n.tgt[k];
 }

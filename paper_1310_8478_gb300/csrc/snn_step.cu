@@ -318,116 +318,130 @@ size_t dense_smem_bytes(uint32_t npc, uint32_t block)
     const size_t warps = block / 32;
     return 2 * kLut * 4                       // LTP / LTD tables
            + (size_t)kSlots * npc * 4         // staged input
-           + warps * 32 * 4 * 3               // per-warp bucket offsets, flags, LTP amounts
-           + (((size_t)kSlots * npc + 15) & ~size_t(15));  // lags (bytes)
+           + warps * 32 * 4 * 2               // per-warp bucket offsets, LTP amounts
+           + (((size_t)kSlots * npc * 2 + 15) & ~size_t(15));  // packed target words
 }
 
+// Packed per-target word of the dense pass, one per staged neuron: bit 15 set
+// when the neuron fired in the previous step (its incoming synapses owe LTP),
+// bits 0..14 the depression an arrival now applies (LTD table at the lag since
+// its last spike; 0 without STDP).  The host enables the dense pass only when
+// every LTD amount fits 15 bits.
+constexpr uint32_t kFiredLast = 0x8000u;
+constexpr uint32_t kDepMask = 0x7fffu;
+
 // One row of the dense pass: the lane takes 8 consecutive synapses per pass,
-// with one 16-byte target load and two 16-byte weight and derivative loads;
-// the delay bucket of each synapse (its deliver flag and LTP amount) is
-// tracked in registers.  kDeriv: the step closes a plasticity period (the
-// long-term update runs between LTP and delivery).
-template <bool kDeriv>
-__device__ __forceinline__ unsigned long long dense_row_walk(const DevNet &n, int64_t base, int m, int D, bool exc,
-                                                             bool stdp, bool ltp_on, uint32_t npc,
-                                                             const int32_t *w_off, const uint32_t *w_flag,
-                                                             const int32_t *w_amt, int32_t *s_in,
-                                                             const uint8_t *s_lag, const int32_t *s_lutm, int lane)
+// with one 16-byte target load and two 16-byte weight and derivative loads.
+// A chunk of 8 lies in one or two delay buckets almost always (buckets hold
+// M / D synapses); the deliver flags (bit d of fbits: the source fired at
+// t - d) and LTP amounts of its positions come from bit masks, and only a
+// chunk spread over three or more buckets walks them position by position.
+// kDeriv: the step closes a plasticity period (the long-term update runs
+// between LTP and delivery) -- excitatory rows only.
+template <bool kExc, bool kDeriv>
+__device__ __forceinline__ void dense_row_walk(const DevNet &n, int64_t base, int m, int D, uint32_t fbits,
+                                               bool stdp, bool ltp_on, const int32_t *w_off, const int32_t *w_amt,
+                                               int32_t *s_in, const uint16_t *s_x, int lane)
 {
     const uint4 *rt4 = reinterpret_cast<const uint4 *>(n.tgt16 + base);
     int4 *rw4 = reinterpret_cast<int4 *>(n.w + base);
     int4 *rs4 = reinterpret_cast<int4 *>(n.sd + base);
-    const bool all_deriv = kDeriv && exc;
-    unsigned visits = 0;
+    // what the row needs at all: its chunks' loads go out before the bucket
+    // search so that the search runs under their latency
+    const bool row_w = kDeriv || fbits != 0;
+    const bool row_sd = kExc && (kDeriv || ltp_on || (stdp && fbits != 0));
     for (int c = lane; c * 8 < m; c += 32) {
         const int k0 = c * 8;
+        const uint4 tv = rt4[c];
+        int4 wa = make_int4(0, 0, 0, 0), wb = wa, sa = wa, sb = wa;
+        if (row_w) {
+            wa = rw4[2 * c];
+            wb = rw4[2 * c + 1];
+        }
+        if (row_sd) {
+            sa = rs4[2 * c];
+            sb = rs4[2 * c + 1];
+        }
         int lo = 1, hi = D;                   // bucket of k0: first d with end > k0
         while (lo < hi) {
             const int mid = (lo + hi) >> 1;
             if (w_off[mid] > k0) hi = mid; else lo = mid + 1;
         }
-        // the current bucket's end, flag and amount stay in registers; a
-        // synapse past the end (rare) moves to the next non-empty bucket
-        int d = lo;
-        int nb = w_off[d];
-        bool fcur = w_flag[d] != 0;
-        int32_t acur = exc ? w_amt[d] : 0;
-        uint32_t vmask = 0, fmask = 0;
+        const int nv = min(8, m - k0);        // valid positions (the row's last chunk is short)
+        const int e0 = w_off[lo];
+        const int n0 = min(e0 - k0, nv);      // positions in bucket lo
+        uint32_t fmask = ((fbits >> lo) & 1u) ? (1u << n0) - 1u : 0u;
+        const int32_t a0 = kExc ? w_amt[lo] : 0;
+        int32_t a1 = 0;
+        int n1 = n0;                          // positions before n1 are in bucket lo or lo + 1
+        if (n0 < nv && w_off[lo + 1] >= k0 + nv) {   // lo < D here: bucket D ends at m
+            n1 = nv;
+            fmask |= ((fbits >> (lo + 1)) & 1u) ? ((1u << nv) - 1u) & ~((1u << n0) - 1u) : 0u;
+            if (kExc) a1 = w_amt[lo + 1];
+        }
         int32_t am[8];
-        bool any_f = false, any_a = false;
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int k = k0 + u;
-            const bool valid = k < m;
-            if (valid && k >= nb) {
-                do {
-                    ++d;
-                } while (k >= w_off[d]);
-                nb = w_off[d];
-                fcur = w_flag[d] != 0;
-                acur = exc ? w_amt[d] : 0;
+        for (int u = 0; u < 8; ++u) am[u] = (u < n0) ? a0 : ((u < nv) ? a1 : 0);
+        if (n1 < nv) {
+            // three or more buckets (or an empty one) inside the chunk
+            int d = lo, nb = e0;
+            fmask = 0;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int k = k0 + u;
+                if (u < nv) {
+                    while (k >= nb) nb = w_off[++d];
+                    fmask |= ((fbits >> d) & 1u) << u;
+                    am[u] = kExc ? w_amt[d] : 0;
+                }
             }
-            vmask |= (valid ? 1u : 0u) << u;
-            fmask |= (valid && fcur ? 1u : 0u) << u;
-            am[u] = valid ? acur : 0;
-            any_f |= valid && fcur;
-            any_a |= am[u] != 0;
-        }
-        const bool need_w = all_deriv || any_f;
-        const bool need_sd = all_deriv || (exc && stdp && any_f) || any_a;
-        if (!need_w && !need_sd) continue;
-        const uint4 tv = rt4[c];
-        int4 wa = make_int4(0, 0, 0, 0), wb = wa, sa = wa, sb = wa;
-        if (need_w) {
-            wa = rw4[2 * c];
-            wb = rw4[2 * c + 1];
-        }
-        if (need_sd) {
-            sa = rs4[2 * c];
-            sb = rs4[2 * c + 1];
         }
         const uint32_t tw[4] = {tv.x, tv.y, tv.z, tv.w};
         int32_t wv[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+        if (!kExc) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const uint32_t v = (u & 1) ? (tw[u >> 1] >> 16) : (tw[u >> 1] & 0xffffu);
+                if ((fmask >> u) & 1u) atomicAdd(&s_in[v], wv[u]);
+            }
+            continue;
+        }
         int32_t sv[8] = {sa.x, sa.y, sa.z, sa.w, sb.x, sb.y, sb.z, sb.w};
-        bool sd_dirty = false;
+        bool sd_dirty = kDeriv;
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
             const bool f = (fmask >> u) & 1u;
-            if (!((vmask >> u) & 1u) || !(f || am[u] || all_deriv)) continue;
             const uint32_t v = (u & 1) ? (tw[u >> 1] >> 16) : (tw[u >> 1] & 0xffffu);
-            const uint32_t idx = (v >> 12) * npc + (v & 0xfffu);
-            if (!exc) {
-                atomicAdd(&s_in[idx], wv[u]);
-                continue;
-            }
-            const int lag = s_lag[idx];
-            const bool pot = am[u] && lag == 1;
-            const int32_t dep = (f && stdp) ? s_lutm[lag] : 0;
-            if (ltp_on && lag == 1) visits++;
+            const uint32_t x = s_x[v];
             int32_t sdv = sv[u];
-            if (pot) sdv += am[u];
-            if (kDeriv) {
+            if ((x & kFiredLast) && am[u]) {
+                sdv += am[u];
+                sd_dirty = true;
+            }
+            if (kDeriv && u < nv) {
                 wv[u] = deriv_w(n, wv[u], sdv);
                 sdv = deriv_sd(n, sdv);
             }
-            if (f) atomicAdd(&s_in[idx], wv[u]);
-            sdv -= dep;
-            sd_dirty |= pot || kDeriv || dep;
+            if (f) {
+                atomicAdd(&s_in[v], wv[u]);
+                const int32_t dep = (int32_t)(x & kDepMask);
+                sdv -= dep;
+                sd_dirty |= dep != 0;
+            }
             sv[u] = sdv;
         }
         if (sd_dirty) {
             rs4[2 * c] = make_int4(sv[0], sv[1], sv[2], sv[3]);
             rs4[2 * c + 1] = make_int4(sv[4], sv[5], sv[6], sv[7]);
         }
-        if (all_deriv) {
+        if (kDeriv) {
             rw4[2 * c] = make_int4(wv[0], wv[1], wv[2], wv[3]);
             rw4[2 * c + 1] = make_int4(wv[4], wv[5], wv[6], wv[7]);
         }
     }
-    return visits;
 }
 
-__global__ void __launch_bounds__(512) k_dense(DevNet n, const int *t_now)
+__global__ void __launch_bounds__(1024) k_dense(DevNet n, const int *t_now)
 {
     extern __shared__ int4 smem_i4[];
     const int t = *t_now;
@@ -438,9 +452,8 @@ __global__ void __launch_bounds__(512) k_dense(DevNet n, const int *t_now)
     int32_t *s_lutm = s_lutp + kLut;
     int32_t *s_in = s_lutm + kLut;                              // [kSlots * npc]
     int32_t *s_off = s_in + kSlots * npc;                       // [nwarps][32] bucket end offsets
-    uint32_t *s_flag = reinterpret_cast<uint32_t *>(s_off + nwarps * 32);  // [nwarps][32] 1: deliver
-    int32_t *s_amt = reinterpret_cast<int32_t *>(s_flag + nwarps * 32);    // [nwarps][32] LTP amount
-    uint8_t *s_lag = reinterpret_cast<uint8_t *>(s_amt + nwarps * 32);     // [kSlots * npc]
+    int32_t *s_amt = s_off + nwarps * 32;                       // [nwarps][32] LTP amount
+    uint16_t *s_x = reinterpret_cast<uint16_t *>(s_amt + nwarps * 32);   // [kSlots * npc] packed words
     __shared__ uint32_t s_col[kSlots];
 
     const bool stdp = !(n.flags & SNN_STDP_OFF);
@@ -453,6 +466,7 @@ __global__ void __launch_bounds__(512) k_dense(DevNet n, const int *t_now)
     const uint32_t r0 = (blockIdx.x - col * chunks) * n.dense_rows;
     const uint32_t r1 = min(npc, r0 + n.dense_rows);
 
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (threadIdx.x < kSlots) s_col[threadIdx.x] = (uint32_t)n.nbr[col * kSlotStride + threadIdx.x];
     for (int i = threadIdx.x; i < kLut; i += blockDim.x) {
         s_lutp[i] = n.lut_p[i];
@@ -461,50 +475,46 @@ __global__ void __launch_bounds__(512) k_dense(DevNet n, const int *t_now)
     __syncthreads();
     for (int sl = 0; sl < kSlots; ++sl) {
         const int32_t *ls = n.last_spike + (size_t)s_col[sl] * npc;
-        uint8_t *lag_row = s_lag + sl * npc;
+        uint16_t *x_row = s_x + sl * npc;
         int32_t *in_row = s_in + sl * npc;
         for (uint32_t loc = threadIdx.x; loc < npc; loc += blockDim.x) {
-            lag_row[loc] = (uint8_t)min(t - ls[loc], 255);
+            const int lag = min(t - ls[loc], 255);
+            x_row[loc] = (uint16_t)((lag == 1 ? kFiredLast : 0u) | (stdp ? (uint32_t)s_lutm[lag] : 0u));
             in_row[loc] = 0;
         }
     }
     __syncthreads();
     drive(n, t, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int32_t *w_off = s_off + warp * 32;
-    uint32_t *w_flag = s_flag + warp * 32;
     int32_t *w_amt = s_amt + warp * 32;
     const int D = (int)n.D;
-    unsigned long long ev_all = 0, ev_exc = 0, visits = 0;
+    const uint32_t dmask = (2u << D) - 2u;            // buckets 1..D
+    unsigned long long ev_all = 0, ev_exc = 0;
     for (uint32_t r = r0 + warp; r < r1; r += nwarps) {
         const uint32_t p = col * npc + r;
         const bool exc = r < n.ne;
         const uint2 hv = n.hl[p];
         const uint32_t h = hv.x;                      // bit k: fired at t - 1 - k
+        const uint32_t fbits = deliver_on ? (h << 1) & dmask : 0u;
         const uint16_t *off = n.doff + (size_t)p * kDoffStride;
         // lane d (1..D) prepares bucket d
         int len = 0;
-        uint32_t fl = 0;
         int32_t amt = 0;
         if (lane >= 1 && lane <= D) {
             const int lo = off[lane - 1], hi = off[lane];
             len = hi - lo;
             w_off[lane] = hi;
-            fl = (deliver_on && ((h >> (lane - 1)) & 1u)) ? 1u : 0u;
             if (exc && ltp_on && len) {
                 const uint32_t recent = h & (0xffffffffu << lane);
                 const int lag = recent ? (__ffs(recent) - 1 - lane) : (t - 1 - (int)hv.y - lane);
                 amt = lag < kLut ? s_lutp[lag] : 0;
             }
-            w_flag[lane] = fl;
             w_amt[lane] = amt;
         }
-        const int delivered = fl ? len : 0;
-        const bool busy = __any_sync(0xffffffffu, fl != 0 || amt != 0) || (exc && deriv_on);
-        int dl = delivered;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) dl += __shfl_xor_sync(0xffffffffu, dl, o);
+        const int delivered = ((fbits >> lane) & 1u) ? len : 0;
+        const bool busy = fbits != 0 || __any_sync(0xffffffffu, amt != 0) || (exc && deriv_on);
+        const int dl = __reduce_add_sync(0xffffffffu, delivered);
         if (lane == 0) {
             ev_all += (unsigned long long)dl;
             if (exc) ev_exc += (unsigned long long)dl;
@@ -513,12 +523,12 @@ __global__ void __launch_bounds__(512) k_dense(DevNet n, const int *t_now)
         if (busy) {
             const int m = off[D];
             const int64_t base = row_base(n, p);     // a multiple of 8: rows are padded
-            if (deriv_on)
-                visits += dense_row_walk<true>(n, base, m, D, exc, stdp, ltp_on, npc, w_off, w_flag, w_amt, s_in,
-                                               s_lag, s_lutm, lane);
+            if (!exc)
+                dense_row_walk<false, false>(n, base, m, D, fbits, stdp, ltp_on, w_off, w_amt, s_in, s_x, lane);
+            else if (deriv_on)
+                dense_row_walk<true, true>(n, base, m, D, fbits, stdp, ltp_on, w_off, w_amt, s_in, s_x, lane);
             else
-                visits += dense_row_walk<false>(n, base, m, D, exc, stdp, ltp_on, npc, w_off, w_flag, w_amt, s_in,
-                                                s_lag, s_lutm, lane);
+                dense_row_walk<true, false>(n, base, m, D, fbits, stdp, ltp_on, w_off, w_amt, s_in, s_x, lane);
         }
         __syncwarp();
     }
@@ -534,7 +544,6 @@ __global__ void __launch_bounds__(512) k_dense(DevNet n, const int *t_now)
     if (lane != 0) ev_all = ev_exc = 0;
     const unsigned long long ba = block_sum(ev_all);
     const unsigned long long be = block_sum(ev_exc);
-    const unsigned long long bv = block_sum(visits);
     if (threadIdx.x == 0) {
         if (ba) {
             atomicAdd(&n.ctr->e_all, ba);
@@ -542,8 +551,10 @@ __global__ void __launch_bounds__(512) k_dense(DevNet n, const int *t_now)
             atomicAdd(&n.ctr->dense_e_all, ba);
             atomicAdd(&n.ctr->dense_e_exc, be);
         }
-        if (bv) atomicAdd(&n.ctr->dense_l_exc, bv);
         if (blockIdx.x == 0) {
+            // potentiation visits: every incoming excitatory synapse of the
+            // neurons that fired at t - 1 (counted when those spikes closed)
+            if (ltp_on) n.ctr->dense_l_exc += n.ctr->l_exc_last;
             n.ctr->dense_steps += 1;
             if (deriv_on) n.ctr->dense_deriv_steps += 1;
         }
@@ -751,6 +762,8 @@ __device__ __forceinline__ void neuron_body(const DevNet &n, const int *t_now, i
     c->step_cnt[par ^ 1][0] = 0;
     c->step_cnt[par ^ 1][1] = 0;
     c->step_cnt[par ^ 1][2] = 0;
+    c->l_exc_last = c->l_exc - c->l_exc_mark;
+    c->l_exc_mark = c->l_exc;
     c->ltp_pending = t;
     c->done_blocks = 0;
     *t_next = t + 1;

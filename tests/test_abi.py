@@ -4,6 +4,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 import workloads
@@ -78,3 +79,14 @@ def test_strerror_covers_every_code():
 
 def test_free_null_is_harmless():
     snn.load().snn_free(None)
+
+
+def test_compact_target_slot_decode_is_exact():
+    """Compact targets store slot * npc + local in 16 bits; the device recovers
+    the slot as (v * ceil(2^31 / npc)) >> 31.  The rounding error of the
+    reciprocal times v < 2^16 stays below 2^-15 < 1 / npc, so the quotient is
+    exact for every column size the compact format admits (npc <= 4096)."""
+    for npc in range(1, 4097):
+        r = np.uint64(((1 << 31) + npc - 1) // npc)
+        v = np.arange(13 * npc, dtype=np.uint64)
+        assert np.array_equal((v * r) >> np.uint64(31), v // np.uint64(npc)), npc
