@@ -300,7 +300,10 @@ int snn_read_profile(snn_net *net, snn_profile *out);
  * snn_save_state / snn_load_state -- checkpoint of the dynamic state (t,
  * neurons, spike history, ring, weights, derivatives, counters, raster step
  * offsets) into / from a host buffer.  Call with host_buf NULL to get the
- * size in *n.  Loading needs a net built from the same configuration.
+ * size in *n.  Loading needs a net built from the same configuration;
+ * SNN_EINVAL (net untouched) for a checkpoint of another configuration or
+ * one that changes an inhibitory weight of a generated net (those synapses
+ * are not plastic).
  */
 int snn_save_state(snn_net *net, void *host_buf, size_t cap, size_t *n);
 int snn_load_state(snn_net *net, const void *host_buf, size_t n);

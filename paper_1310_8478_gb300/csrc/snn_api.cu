@@ -919,6 +919,7 @@ int snn_build_network(const snn_config *cfg, void *cuda_stream, size_t hbm_budge
     if ((r = cuda_init(net, cuda_stream)) != SNN_OK) return fail(r);
     if ((r = alloc_common(net)) != SNN_OK) return fail(r);
     net->dn.uniform_m = m_store;
+    net->dn.w_inh = c.w_inh0_q16;
     net->dn.canon_m = c.fanout;
     net->wrange = WeightRange{c.w_exc0_q16, c.w_exc0_q16, c.w_inh0_q16, c.w_inh0_q16};
     GenParams &g = net->gen;
@@ -1706,6 +1707,24 @@ int snn_load_state(snn_net *net, const void *host_buf, size_t n)
         return SNN_EINVAL;
     }
     const char *p = (const char *)host_buf + sizeof h;
+    if (!net->explicit_net) {
+        // inhibitory synapses are not plastic: a checkpoint of this net keeps
+        // their weight, and the dense pass relies on it
+        const char *wb = p + N * (16 + 2 * fsz) + D * N * 4 + D * 8;
+        const size_t stride = net->dn.uniform_m, m = net->dn.canon_m, npc = net->cfg.neurons_per_col;
+        for (size_t q = 0; q < N; ++q) {
+            if (q % npc < net->cfg.exc_per_col) continue;
+            for (size_t j = 0; j < m; ++j) {
+                int32_t w;
+                std::memcpy(&w, wb + (q * stride + j) * 4, 4);
+                if (w != net->dn.w_inh) {
+                    set_error("checkpoint changes the weight of inhibitory synapse %zu of neuron %zu, "
+                              "which is not plastic", j, q);
+                    return SNN_EINVAL;
+                }
+            }
+        }
+    }
     cudaStream_t s = net->stream;
     DevNet &dn = net->dn;
     void *sv = dn.vd ? (void *)dn.vd : (void *)dn.v;

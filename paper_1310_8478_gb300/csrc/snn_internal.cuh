@@ -42,6 +42,8 @@ struct DevCounters {
 struct DevNet {
     uint32_t N, npc, ne, C, D;       // neurons, per column, excitatory per column, columns, max delay
     uint32_t D_inh;                  // largest delay of an inhibitory synapse (1 for generated nets)
+    int32_t w_inh;                   // generated nets: the weight of every inhibitory synapse (not
+                                     //                 plastic); the dense pass reads no inhibitory w
     uint32_t uniform_m;              // > 0: row p starts at p * uniform_m (generated nets; the
                                      //       row stride, a multiple of 8 for compact targets)
     uint32_t canon_m;                // generated nets: synapses per row (the fan-out M)

@@ -339,7 +339,7 @@ constexpr uint32_t kDepMask = 0x7fffu;
 // kDeriv: the step closes a plasticity period (the long-term update runs
 // between LTP and delivery) -- excitatory rows only.
 template <bool kExc, bool kDeriv>
-__device__ __forceinline__ void dense_row_walk(const DevNet &n, int64_t base, int m, int D, uint32_t fbits,
+__device__ __forceinline__ void dense_row_walk(const DevNet &n, int64_t base, int m, int D, float scale, uint32_t fbits,
                                                bool stdp, bool ltp_on, const int32_t *w_off, const int32_t *w_amt,
                                                int32_t *s_in, const uint16_t *s_x, int lane)
 {
@@ -362,11 +362,11 @@ __device__ __forceinline__ void dense_row_walk(const DevNet &n, int64_t base, in
             sa = rs4[2 * c];
             sb = rs4[2 * c + 1];
         }
-        int lo = 1, hi = D;                   // bucket of k0: first d with end > k0
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (w_off[mid] > k0) hi = mid; else lo = mid + 1;
-        }
+        // bucket of k0 (first d with end > k0): delays are near uniform along
+        // a row, so the interpolated guess is right or one off almost always
+        int lo = min(D, 1 + (int)((float)k0 * scale));
+        while (w_off[lo] <= k0) ++lo;         // bucket D ends at m > k0
+        while (w_off[lo - 1] > k0) --lo;      // w_off[0] = 0 <= k0
         const int nv = min(8, m - k0);        // valid positions (the row's last chunk is short)
         const int e0 = w_off[lo];
         const int n0 = min(e0 - k0, nv);      // positions in bucket lo
@@ -501,6 +501,7 @@ __global__ void __launch_bounds__(1024) k_dense(DevNet n, const int *t_now)
         // lane d (1..D) prepares bucket d
         int len = 0;
         int32_t amt = 0;
+        if (lane == 0) w_off[0] = 0;
         if (lane >= 1 && lane <= D) {
             const int lo = off[lane - 1], hi = off[lane];
             len = hi - lo;
@@ -520,15 +521,33 @@ __global__ void __launch_bounds__(1024) k_dense(DevNet n, const int *t_now)
             if (exc) ev_exc += (unsigned long long)dl;
         }
         __syncwarp();
-        if (busy) {
+        if (!exc && n.D_inh == 1) {
+            // inhibitory row of a generated net: one bucket (delay 1), one
+            // weight, nothing plastic
+            if (fbits & 2u) {
+                const int m = off[D];
+                const uint4 *rt4 = reinterpret_cast<const uint4 *>(n.tgt16 + row_base(n, p));
+                for (int c = lane; c * 8 < m; c += 32) {
+                    const uint4 tv = rt4[c];
+                    const int nv = min(8, m - c * 8);
+                    const uint32_t tw[4] = {tv.x, tv.y, tv.z, tv.w};
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const uint32_t v = (u & 1) ? (tw[u >> 1] >> 16) : (tw[u >> 1] & 0xffffu);
+                        if (u < nv) atomicAdd(&s_in[v], n.w_inh);
+                    }
+                }
+            }
+        } else if (busy) {
             const int m = off[D];
+            const float scale = (float)D / (float)m;
             const int64_t base = row_base(n, p);     // a multiple of 8: rows are padded
             if (!exc)
-                dense_row_walk<false, false>(n, base, m, D, fbits, stdp, ltp_on, w_off, w_amt, s_in, s_x, lane);
+                dense_row_walk<false, false>(n, base, m, D, scale, fbits, stdp, ltp_on, w_off, w_amt, s_in, s_x, lane);
             else if (deriv_on)
-                dense_row_walk<true, true>(n, base, m, D, fbits, stdp, ltp_on, w_off, w_amt, s_in, s_x, lane);
+                dense_row_walk<true, true>(n, base, m, D, scale, fbits, stdp, ltp_on, w_off, w_amt, s_in, s_x, lane);
             else
-                dense_row_walk<true, false>(n, base, m, D, fbits, stdp, ltp_on, w_off, w_amt, s_in, s_x, lane);
+                dense_row_walk<true, false>(n, base, m, D, scale, fbits, stdp, ltp_on, w_off, w_amt, s_in, s_x, lane);
         }
         __syncwarp();
     }

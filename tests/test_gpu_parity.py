@@ -254,6 +254,36 @@ def test_checkpoint_resume_is_bitexact(eng, mode):
         assert np.array_equal(w[0], ref_w[0]) and np.array_equal(w[1], ref_w[1])
 
 
+def test_checkpoint_changing_an_inhibitory_weight_is_rejected(eng):
+    """Inhibitory synapses are not plastic (Sec. 2 "Synaptic update": STDP acts
+    on excitatory synapses); a checkpoint that changes one is refused."""
+    from paper_1310_8478_gb300 import snn
+    cfg = workloads.custom(grid_x=2, grid_y=2, fanout=100, pct_ring=(40, 30, 20, 10), seed=63)
+    with gpu_net(eng, cfg) as a:
+        a.run(50)
+        blob = bytearray(a.save_state())
+    # the first inhibitory row's weights: the first run of 100 equal values
+    # w_inh0 in the buffer (excitatory rows, currents and state hold none)
+    w_inh = np.int32(cfg["w_inh0_q16"])
+    hit = None
+    for shift in range(4):
+        v = np.frombuffer(bytes(blob[shift:len(blob) - (len(blob) - shift) % 4]), dtype=np.int32)
+        eq = np.concatenate([[0], (v == w_inh).astype(np.int8), [0]])
+        d = np.diff(eq)
+        starts, ends = np.flatnonzero(d == 1), np.flatnonzero(d == -1)
+        runs = [(s0, e0) for s0, e0 in zip(starts, ends) if e0 - s0 >= 100]
+        if runs:
+            off = shift + 4 * int(runs[0][0])
+            hit = off if hit is None else min(hit, off)
+    assert hit is not None
+    with gpu_net(eng, cfg) as b:
+        b.load_state(bytes(blob))                      # unchanged: accepted
+        blob[hit:hit + 4] = np.int32(w_inh + 1).tobytes()
+        with pytest.raises(snn.SnnError) as e:
+            b.load_state(bytes(blob))
+        assert e.value.code == snn.EINVAL
+
+
 def test_run_host_equals_run_and_raster(eng):
     cfg = workloads.custom(grid_x=2, grid_y=2, fanout=100, pct_ring=(40, 30, 20, 10), seed=62)
     with gpu_net(eng, cfg) as a, gpu_net(eng, cfg, "dense") as b:
