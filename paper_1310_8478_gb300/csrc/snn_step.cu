@@ -491,19 +491,33 @@ __global__ void __launch_bounds__(1024) k_dense(DevNet n, const int *t_now)
     const int D = (int)n.D;
     const uint32_t dmask = (2u << D) - 2u;            // buckets 1..D
     unsigned long long ev_all = 0, ev_exc = 0;
+    // row metadata goes out one row ahead: the spike-history word and, in lane
+    // d <= D, the end of delay bucket d
+    uint2 hv_next = make_uint2(0u, 0u);
+    int off_next = 0;
+    if (r0 + warp < r1) {
+        const uint32_t p = col * npc + r0 + warp;
+        hv_next = n.hl[p];
+        off_next = (lane <= D) ? (int)n.doff[(size_t)p * kDoffStride + lane] : 0;
+    }
     for (uint32_t r = r0 + warp; r < r1; r += nwarps) {
         const uint32_t p = col * npc + r;
         const bool exc = r < n.ne;
-        const uint2 hv = n.hl[p];
+        const uint2 hv = hv_next;
+        const int hi = off_next;
+        if (r + nwarps < r1) {
+            hv_next = n.hl[p + nwarps];
+            off_next = (lane <= D) ? (int)n.doff[(size_t)(p + nwarps) * kDoffStride + lane] : 0;
+        }
         const uint32_t h = hv.x;                      // bit k: fired at t - 1 - k
         const uint32_t fbits = deliver_on ? (h << 1) & dmask : 0u;
-        const uint16_t *off = n.doff + (size_t)p * kDoffStride;
+        const int lo = __shfl_up_sync(0xffffffffu, hi, 1);
+        const int m = __shfl_sync(0xffffffffu, hi, D);
         // lane d (1..D) prepares bucket d
         int len = 0;
         int32_t amt = 0;
         if (lane == 0) w_off[0] = 0;
         if (lane >= 1 && lane <= D) {
-            const int lo = off[lane - 1], hi = off[lane];
             len = hi - lo;
             w_off[lane] = hi;
             if (exc && ltp_on && len) {
@@ -525,7 +539,6 @@ __global__ void __launch_bounds__(1024) k_dense(DevNet n, const int *t_now)
             // inhibitory row of a generated net: one bucket (delay 1), one
             // weight, nothing plastic
             if (fbits & 2u) {
-                const int m = off[D];
                 const uint4 *rt4 = reinterpret_cast<const uint4 *>(n.tgt16 + row_base(n, p));
                 for (int c = lane; c * 8 < m; c += 32) {
                     const uint4 tv = rt4[c];
@@ -539,7 +552,6 @@ __global__ void __launch_bounds__(1024) k_dense(DevNet n, const int *t_now)
                 }
             }
         } else if (busy) {
-            const int m = off[D];
             const float scale = (float)D / (float)m;
             const int64_t base = row_base(n, p);     // a multiple of 8: rows are padded
             if (!exc)
