@@ -283,7 +283,8 @@ size_t footprint(const snn_config *c, uint32_t N, int64_t S, int64_t n_rin, bool
 {
     const size_t D = c->max_delay_ms;
     size_t b = 0;
-    b += (size_t)S * ((!explicit_net && c->neurons_per_col <= kMaxCompactNpc) ? 10 : 12);  // tgt, w, sd
+    b += (size_t)S * ((!explicit_net && c->neurons_per_col >= kMinCompactNpc && c->neurons_per_col <= kMaxCompactNpc)
+                          ? 10 : 12);  // tgt, w, sd
     b += (size_t)c->grid_x * c->grid_y * kSlotStride * 4;                                  // neighbour table
     b += (size_t)N * kDoffStride * 2;             // delay offsets
     b += ((size_t)N + 1) * 8 * 2;                 // row_off, rin_off
@@ -309,7 +310,8 @@ int alloc_common(snn_net *net)
     const uint32_t N = net->N;
     const uint32_t D = net->cfg.max_delay_ms;
     DevNet &dn = net->dn;
-    const bool compact = !net->explicit_net && net->cfg.neurons_per_col <= kMaxCompactNpc;
+    const bool compact = !net->explicit_net && net->cfg.neurons_per_col >= kMinCompactNpc &&
+                         net->cfg.neurons_per_col <= kMaxCompactNpc;
     if (compact) SNN_TRY(dalloc_t(net, (size_t)net->S_store, &net->tgt16));
     else SNN_TRY(dalloc_t(net, (size_t)net->S_store, &net->tgt));
     const uint32_t C = net->cfg.grid_x * net->cfg.grid_y;
@@ -356,7 +358,9 @@ int alloc_common(snn_net *net)
     dn.doff = net->doff;
     dn.tgt = net->tgt;
     dn.tgt16 = net->tgt16;
-    dn.npc_recip = (uint32_t)(((1ull << 31) + net->cfg.neurons_per_col - 1) / net->cfg.neurons_per_col);
+    dn.npc_recip = net->cfg.neurons_per_col >= kMinCompactNpc
+                       ? (uint32_t)(((1ull << 32) + net->cfg.neurons_per_col - 1) / net->cfg.neurons_per_col)
+                       : 0u;
     dn.nbr = net->nbr;
     dn.w = net->w;
     dn.sd = net->sd;
@@ -907,7 +911,7 @@ int snn_build_network(const snn_config *cfg, void *cuda_stream, size_t hbm_budge
     if (r != SNN_OK) return fail(r);
     const snn_config &c = net->cfg;
     net->S = (int64_t)net->N * c.fanout;
-    const bool compact = c.neurons_per_col <= kMaxCompactNpc;
+    const bool compact = c.neurons_per_col >= kMinCompactNpc && c.neurons_per_col <= kMaxCompactNpc;
     const uint32_t m_store = compact ? ((c.fanout + 7u) & ~7u) : c.fanout;
     net->S_store = (int64_t)net->N * m_store;
     const int64_t n_rin_est = (int64_t)c.grid_x * c.grid_y * c.exc_per_col * c.fanout;

@@ -18,6 +18,7 @@ constexpr int kSlots = 13;           // own column + 3 rings of 4 neighbour colu
 constexpr int kSlotStride = 16;      // entries per column in the neighbour table
 constexpr int32_t kNoPending = -(1 << 30);  // ltp_pending value when no LTP is owed
 constexpr uint32_t kMaxCompactNpc = 4096;    // compact targets slot * npc + local stay below 2^16
+constexpr uint32_t kMinCompactNpc = 2;       // the slot reciprocal ceil(2^32 / npc) fits 32 bits
 constexpr uint32_t kDenseMaxNpc = 2800;      // staged columns must fit in shared memory
 static_assert(kSlots * kMaxCompactNpc <= 65536, "compact targets must fit 16 bits");
 constexpr int kUnroll = 4;                   // dense pass: positions per lane in flight
@@ -52,7 +53,7 @@ struct DevNet {
     const uint16_t *doff;            // [N][kDoffStride]: synapses of delay <= d, d = 0..D
     int32_t *tgt;                    // [S] target gid (explicit nets / big columns), or NULL
     uint16_t *tgt16;                 // [S] compact target: slot * npc + local id, or NULL
-    uint32_t npc_recip;              // ceil(2^31 / npc): slot = (v * npc_recip) >> 31 for v < 2^16
+    uint32_t npc_recip;              // ceil(2^32 / npc): slot = umulhi(v, npc_recip) for v < 2^16
     const int32_t *nbr;              // [C][kSlotStride] global column of every slot
     int32_t *w, *sd;                 // [S] weight, STDP derivative; rows sorted by delay
     const int64_t *rin_off;          // [N + 1] reverse index (incoming excitatory synapses)
@@ -210,7 +211,7 @@ __device__ __forceinline__ uint32_t target_gid(const DevNet &n, uint32_t src_col
 {
     if (n.tgt16) {
         const uint32_t v = n.tgt16[k];
-        const uint32_t slot = (uint32_t)(((uint64_t)v * n.npc_recip) >> 31);
+        const uint32_t slot = __umulhi(v, n.npc_recip);
         return (uint32_t)n.nbr[src_col * kSlotStride + slot] * n.npc + (v - slot * n.npc);
     }
     return (uint32_t)n.tgt[k];

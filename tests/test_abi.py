@@ -83,10 +83,11 @@ def test_free_null_is_harmless():
 
 def test_compact_target_slot_decode_is_exact():
     """Compact targets store slot * npc + local in 16 bits; the device recovers
-    the slot as (v * ceil(2^31 / npc)) >> 31.  The rounding error of the
-    reciprocal times v < 2^16 stays below 2^-15 < 1 / npc, so the quotient is
-    exact for every column size the compact format admits (npc <= 4096)."""
-    for npc in range(1, 4097):
-        r = np.uint64(((1 << 31) + npc - 1) // npc)
+    the slot as the high word of v * ceil(2^32 / npc).  The rounding error of
+    the reciprocal times v < 2^16 stays below 2^-16 < 1 / npc, so the quotient
+    is exact for every column size the compact format admits (2 <= npc <= 4096)."""
+    for npc in range(2, 4097):
+        r = np.uint64(((1 << 32) + npc - 1) // npc)
+        assert r < 2 ** 32
         v = np.arange(13 * npc, dtype=np.uint64)
-        assert np.array_equal((v * r) >> np.uint64(31), v // np.uint64(npc)), npc
+        assert np.array_equal((v * r) >> np.uint64(32), v // np.uint64(npc)), npc
