@@ -336,6 +336,13 @@ def main():
     K, W = args.steps, args.warmup
     n_neurons = workloads.n_neurons(cfg)
     raster_cap = int(n_neurons * (K + W + 2) * 0.8) + (1 << 20)
+    # the raster takes what the net leaves of the device (net: 10 B per
+    # synapse slot, 12 B per reverse entry, ~200 B per neuron), so that a
+    # large net over many steps still builds; a full raster counts its drops
+    n_rin = cfg["grid_x"] * cfg["grid_y"] * cfg["exc_per_col"] * cfg["fanout"]
+    net_est = workloads.n_synapses(cfg) * 10 + n_rin * 12 + n_neurons * 200
+    free = torch.cuda.mem_get_info()[0]
+    raster_cap = max(1 << 20, min(raster_cap, (free - net_est - (8 << 30)) // 4))
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         t_build = time.perf_counter()
@@ -474,6 +481,7 @@ def main():
         "wall_s_per_sim_s": secs / (K / 1000.0),
         "rate_hz": rate_hz,
         "events": d_events, "spikes": d_spikes,
+        "raster": {"capacity": raster_cap, "dropped": c1["raster_dropped"]},
         "roofline": roofline,
         "kernels": per_kernel,
         "gpu_launches": int(sum(prof[k][0] for k in names)),
