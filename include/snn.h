@@ -123,6 +123,11 @@ typedef struct {
     uint32_t dense_rows;             /* source rows per block of the dense pass */
     uint32_t dense_permille;         /* a step takes the dense pass when at least this many
                                         neurons per 1000 fired in the step before; 1001 = never */
+    uint32_t staged_permille;        /* a step without the dense pass delivers column by column
+                                        through shared memory when its expected events (spikes of
+                                        the last max_delay steps x fan-out / max_delay, plus
+                                        inhibitory spikes of the step before x fan-out) reach this
+                                        many per 1000 neurons; 0xffffffff = never */
 } snn_launch;
 
 /* Per-kernel device time collected while profiling is on (CUDA events), and

@@ -109,6 +109,8 @@ struct snn_net {
     int32_t *nbr = nullptr;
     bool ltp_owed = false;          // the last step's LTP has not been applied yet
     bool dense_ok = false;          // the dense pass can run on this net
+    int dense_grid = 0;             // blocks of the dense pass (at most one wave of resident blocks)
+    int staged_grid = 0;            // blocks of the column-staged delivery (likewise)
     uint64_t version = 0;           // bumped whenever captured launches go stale
     // stimulus
     size_t stim_cap = 0;
@@ -385,19 +387,34 @@ int alloc_common(snn_net *net)
     return SNN_OK;
 }
 
-// whether the dense pass can run with the current launch shape (shared memory)
+// whether the dense pass and the column-staged delivery can run with the
+// current launch shape (compact targets, shared memory)
 int setup_dense(snn_net *net)
 {
     net->dense_ok = false;
+    net->dn.staged_ok = 0;
+    net->dn.staged_min_events = ~0ull;
     if (!net->tgt16 || net->cfg.neurons_per_col > kDenseMaxNpc) return SNN_OK;
-    // the dense pass packs each depression amount into 15 bits
+    // both stage each depression amount in 15 bits
     std::vector<int32_t> lut;
     if (build_luts(&net->cfg, lut) != SNN_OK) return SNN_OK;
     for (int k = 0; k < kLut; ++k)
         if (lut[kLut + k] < 0 || lut[kLut + k] > 0x7fff) return SNN_OK;
-    const size_t bytes = dense_smem_bytes(net->cfg.neurons_per_col, net->launch.dense_block);
     int optin = 0;
     SNN_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, net->device));
+    const size_t sbytes = staged_smem_bytes(net->cfg.neurons_per_col, kStagedBlock);
+    if (sbytes + 1024 <= (size_t)optin) {
+        SNN_CUDA(cudaFuncSetAttribute(k_deliver_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sbytes));
+        int per_sm = 0;
+        SNN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_deliver_cols, (int)kStagedBlock, sbytes));
+        if (per_sm >= 1) {
+            net->dn.staged_ok = 1;
+            net->staged_grid = (int)std::min<int64_t>(net->dn.C, (int64_t)per_sm * net->sm_count);
+            const uint32_t pm = net->launch.staged_permille;
+            net->dn.staged_min_events = pm == 0xffffffffu ? ~0ull : (unsigned long long)net->N * pm / 1000ull;
+        }
+    }
+    const size_t bytes = dense_smem_bytes(net->cfg.neurons_per_col, net->launch.dense_block);
     if (bytes + 1024 > (size_t)optin) return SNN_OK;
     SNN_CUDA(cudaFuncSetAttribute(k_dense, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
     int per_sm = 0;
@@ -414,6 +431,8 @@ int setup_dense(snn_net *net)
         rows = (npc + chunks - 1) / chunks;
     }
     net->dn.dense_rows = rows;
+    const int64_t units = (int64_t)net->dn.C * ((net->cfg.neurons_per_col + rows - 1) / rows);
+    net->dense_grid = (int)std::min<int64_t>(units, (int64_t)per_sm * net->sm_count);
     net->dense_ok = true;
     return SNN_OK;
 }
@@ -522,6 +541,7 @@ int start_net(const snn_config *cfg, void *cuda_stream, size_t budget, snn_net *
     net->launch.dense_block = 512;
     net->launch.dense_rows = 0;
     net->launch.dense_permille = 50;
+    net->launch.staged_permille = 10000;
     (void)cuda_stream;
     return SNN_OK;
 }
@@ -618,11 +638,12 @@ void launch_step(snn_net *net, int32_t t, cudaStream_t s)
     }
     mark(0);
     k_deliver<<<g_del, L.deliver_block, 0, s>>>(dn, t_now);
+    if (dn.staged_ok)
+        k_deliver_cols<<<net->staged_grid, kStagedBlock, staged_smem_bytes(dn.npc, kStagedBlock), s>>>(dn, t_now);
     mark(0);
     if (net->dense_ok) {
-        const uint32_t chunks = (dn.npc + dn.dense_rows - 1) / dn.dense_rows;
         mark(4);
-        k_dense<<<dn.C * chunks, L.dense_block, dense_smem_bytes(dn.npc, L.dense_block), s>>>(dn, t_now);
+        k_dense<<<net->dense_grid, L.dense_block, dense_smem_bytes(dn.npc, L.dense_block), s>>>(dn, t_now);
         mark(4);
     }
     // [S2(t) S3(t)]
@@ -1073,6 +1094,7 @@ int snn_set_launch(snn_net *net, const snn_launch *launch)
     L.dense_block = pick(launch->dense_block, L.dense_block);
     L.dense_rows = pick(launch->dense_rows, L.dense_rows);
     L.dense_permille = pick(launch->dense_permille, L.dense_permille);
+    L.staged_permille = pick(launch->staged_permille, L.staged_permille);
     for (uint32_t b : {L.deliver_block, L.neuron_block, L.ltp_block, L.deriv_block}) {
         if (b < 32 || b > 1024 || b % 32) { set_error("block sizes must be multiples of 32 in 32..1024"); return SNN_EINVAL; }
     }
@@ -1752,6 +1774,8 @@ int snn_load_state(snn_net *net, const void *host_buf, size_t n)
     hc.t_slot[h.t & 1] = h.t;
     hc.ltp_pending = kNoPending;
     hc.done_blocks = 0;
+    hc.dense_cursor = 0;
+    hc.staged_cursor = 0;
     SNN_CUDA(cudaMemcpyAsync(net->ctr, &hc, sizeof hc, cudaMemcpyHostToDevice, s));
     if (dn.raster_step_off) SNN_CUDA(cudaMemsetAsync(dn.raster_step_off, 0, 8, s));
     SNN_CUDA(cudaStreamSynchronize(s));

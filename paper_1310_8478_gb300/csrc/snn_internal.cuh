@@ -37,12 +37,16 @@ struct DevCounters {
     unsigned long long dense_steps, dense_deriv_steps;
     unsigned long long l_exc_mark;   // l_exc when the last step closed
     unsigned long long l_exc_last;   // excitatory in-degree of the neurons that fired in the last step
+    unsigned dense_cursor;           // work units of the dense pass handed out in this step
+    unsigned staged_cursor;          // columns of the column-staged delivery handed out in this step
 };
 
 // Everything a step kernel needs, passed by value.
 struct DevNet {
     uint32_t N, npc, ne, C, D;       // neurons, per column, excitatory per column, columns, max delay
     uint32_t D_inh;                  // largest delay of an inhibitory synapse (1 for generated nets)
+    int staged_ok;                   // the column-staged delivery may run (compact targets, staging fits)
+    unsigned long long staged_min_events;   // it runs when a step's expected events reach this
     int32_t w_inh;                   // generated nets: the weight of every inhibitory synapse (not
                                      //                 plastic); the dense pass reads no inhibitory w
     uint32_t uniform_m;              // > 0: row p starts at p * uniform_m (generated nets; the
@@ -225,6 +229,20 @@ __device__ __forceinline__ bool dense_selected(const DevNet &n, int t)
     return (uint32_t)(n.ring_cnt[2 * slot] + n.ring_cnt[2 * slot + 1]) >= n.dense_min_spikes;
 }
 
+// a step without the dense pass delivers column by column through shared
+// memory when its expected events reach staged_min_events: excitatory spikes
+// of t - d reach bucket d (about M / D synapses), inhibitory spikes of t - 1
+// their whole row (generated nets: inhibitory delay 1)
+__device__ __forceinline__ bool staged_selected(const DevNet &n, int t)
+{
+    if (!n.staged_ok || t < 1 || dense_selected(n, t)) return false;
+    unsigned long long exc = 0;
+    for (int d = 1; d <= (int)n.D && d <= t; ++d) exc += (unsigned)n.ring_cnt[2 * ((t - d) % (int)n.D)];
+    const unsigned long long inh = (unsigned)n.ring_cnt[2 * ((t - 1) % (int)n.D) + 1];
+    const unsigned long long est = exc * n.canon_m / n.D + inh * n.canon_m;
+    return est >= n.staged_min_events;
+}
+
 __device__ __forceinline__ int64_t row_base(const DevNet &n, uint32_t p)
 {
     return n.uniform_m ? (int64_t)p * n.uniform_m : n.row_off[p];
@@ -265,6 +283,7 @@ __global__ void k_read_rows(DevNet n, GenParams g, const uint8_t *canon_delay, u
 
 __global__ void k_deliver(DevNet n, const int *t_now);
 __global__ void k_dense(DevNet n, const int *t_now);
+__global__ void k_deliver_cols(DevNet n, const int *t_now);
 __global__ void k_neuron_f32(DevNet n, const int *t_now, int *t_next);
 __global__ void k_neuron_f64(DevNet n, const int *t_now, int *t_next);
 __global__ void k_probe(DevNet n, const int *t_now);
@@ -273,5 +292,7 @@ __global__ void k_deriv(DevNet n, const int *t_now, int force);
 __global__ void k_fold(DevNet n, const int *t_now, int force);
 
 size_t dense_smem_bytes(uint32_t npc, uint32_t block);
+size_t staged_smem_bytes(uint32_t npc, uint32_t block);
+constexpr uint32_t kStagedBlock = 512;      // threads per block of the column-staged delivery
 
 }  // namespace snn

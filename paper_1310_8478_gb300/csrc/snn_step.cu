@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(1024) k_deliver(DevNet n, const int *t_now)
     __shared__ int s_tile_start[32 * 33];        // per warp: prefix of the items' lengths
     __shared__ uint32_t s_tile_info[32 * 32];    // per warp: kind and source column of each item
     const int t = *t_now;
-    if (dense_selected(n, t)) return;
+    if (dense_selected(n, t) || staged_selected(n, t)) return;
     const bool stdp = !(n.flags & SNN_STDP_OFF);
     const int nl = (int)(n.D + n.D_inh);
     for (int i = threadIdx.x; i < kLut; i += blockDim.x) s_lut[i] = n.lut_m[i];
@@ -203,6 +203,156 @@ __global__ void __launch_bounds__(1024) k_deliver(DevNet n, const int *t_now)
             }
         }
         __syncwarp();
+    }
+    if (lane != 0) ev_all = ev_exc = 0;
+    const unsigned long long ba = block_sum(ev_all);
+    const unsigned long long be = block_sum(ev_exc);
+    if (threadIdx.x == 0 && ba) {
+        atomicAdd(&n.ctr->e_all, ba);
+        atomicAdd(&n.ctr->e_exc, be);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// sparse S1, column by column (generated nets with compact targets, in steps
+// with many events): block per source column.  The 13 columns its synapses
+// reach are staged in shared memory -- the input accumulator and the LTD
+// amount at each neuron's current lag -- so that an event costs a shared
+// atomic and a shared load instead of a random L2 reduction and a random
+// gather.  A warp scans 32 rows at a time, turns every delay bucket d whose
+// source fired at t - d into an item, and walks the concatenated synapses of
+// 32 items with all lanes; the input is flushed with one coalesced reduction
+// per touched neuron.
+// ---------------------------------------------------------------------------
+constexpr int kTileWords = 32 + 33 + 32;     // per warp: item starts, length prefix, kinds
+
+size_t staged_smem_bytes(uint32_t npc, uint32_t block)
+{
+    return (size_t)kLut * 4 + (size_t)kSlots * npc * 4 + (size_t)(block / 32) * kTileWords * 4 +
+           (((size_t)kSlots * npc * 2 + 15) & ~size_t(15));
+}
+
+__global__ void __launch_bounds__(kStagedBlock) k_deliver_cols(DevNet n, const int *t_now)
+{
+    extern __shared__ int4 smem_i4[];
+    __shared__ uint32_t s_col[kSlots];
+    const int t = *t_now;
+    if (!staged_selected(n, t)) return;
+    const uint32_t npc = n.npc;
+    const uint32_t nwarps = blockDim.x >> 5;
+    int32_t *s_lut = reinterpret_cast<int32_t *>(smem_i4);
+    int32_t *s_in = s_lut + kLut;                                        // [kSlots * npc]
+    int32_t *s_tile = s_in + kSlots * npc;                               // [nwarps][kTileWords]
+    uint16_t *s_x = reinterpret_cast<uint16_t *>(s_tile + nwarps * kTileWords);   // [kSlots * npc]
+    const bool stdp = !(n.flags & SNN_STDP_OFF);
+    const bool deliver_on = !(n.flags & SNN_DELIVERY_OFF);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < kLut; i += blockDim.x) s_lut[i] = n.lut_m[i];
+    drive(n, t, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+    const int D = (int)n.D;
+    const uint32_t dmask_e = (2u << D) - 2u, dmask_i = (2u << n.D_inh) - 2u;
+    int32_t *w_lo = s_tile + warp * kTileWords;                // [32] column-relative first synapse
+    int32_t *w_start = w_lo + 32;                              // [33] prefix of the lengths
+    int32_t *w_exc = w_start + 33;                             // [32] 1: excitatory row
+    unsigned long long ev_all = 0, ev_exc = 0;
+    // the grid is at most one wave of resident blocks; a block takes columns
+    // from a step-wide cursor
+    __shared__ uint32_t s_unit;
+    for (uint32_t col = blockIdx.x; col < n.C;) {
+        if (threadIdx.x < kSlots) s_col[threadIdx.x] = (uint32_t)n.nbr[col * kSlotStride + threadIdx.x];
+        __syncthreads();
+        // the LTD amount (at most 15 bits: the host checks the table) of every
+        // staged neuron at its lag t - last_spike >= 1, saturated at the table end
+        for (int sl = 0; sl < kSlots; ++sl) {
+            const int32_t *ls = n.last_spike + (size_t)s_col[sl] * npc;
+            uint16_t *x_row = s_x + sl * npc;
+            int32_t *in_row = s_in + sl * npc;
+            for (uint32_t loc = threadIdx.x; loc < npc; loc += blockDim.x) {
+                x_row[loc] = stdp ? (uint16_t)s_lut[min(t - ls[loc], kLut - 1)] : (uint16_t)0;
+                in_row[loc] = 0;
+            }
+        }
+        __syncthreads();
+        const int64_t cbase = (int64_t)col * npc * n.uniform_m;   // first synapse of the column
+        for (uint32_t rb = warp * 32; rb < npc; rb += nwarps * 32) {
+            const uint32_t r = rb + lane;
+            uint32_t fb = 0;                                       // bit d: the row's source fired at t - d
+            if (r < npc && deliver_on) fb = (n.hl[col * npc + r].x << 1) & (r < n.ne ? dmask_e : dmask_i);
+            while (__any_sync(0xffffffffu, fb != 0)) {
+                // every lane takes the lowest flagged bucket of its row
+                const int d = fb ? __ffs(fb) - 1 : 0;
+                fb &= fb - 1u;
+                int len = 0, lo = 0, exc = 0;
+                if (d) {
+                    const uint16_t *off = n.doff + (size_t)(col * npc + r) * kDoffStride;
+                    const int a = off[d - 1];
+                    len = (int)off[d] - a;
+                    lo = (int)(r * n.uniform_m) + a;
+                    exc = r < n.ne ? 1 : 0;
+                }
+                int incl = len;
+    #pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                const int tile_len = __shfl_sync(0xffffffffu, incl, 31);
+                const int exc_len = __reduce_add_sync(0xffffffffu, exc ? len : 0);
+                w_lo[lane] = lo;
+                w_start[lane] = incl - len;
+                w_exc[lane] = exc;
+                if (lane == 0) {
+                    w_start[32] = tile_len;
+                    ev_all += (unsigned long long)tile_len;
+                    ev_exc += (unsigned long long)exc_len;
+                }
+                __syncwarp();
+                // kUnroll synapses per lane in flight: targets, weights and
+                // derivatives first, then the staged updates
+                int j = 0;
+                for (int e0 = lane; e0 < tile_len; e0 += 32 * kUnroll) {
+                    int64_t k[kUnroll];
+                    uint32_t v[kUnroll];
+                    int32_t wk[kUnroll], sk[kUnroll];
+                    bool ex[kUnroll];
+    #pragma unroll
+                    for (int u = 0; u < kUnroll; ++u) {
+                        const int e = e0 + 32 * u;
+                        k[u] = -1;
+                        if (e < tile_len) {
+                            while (w_start[j + 1] <= e) ++j;
+                            k[u] = cbase + w_lo[j] + (e - w_start[j]);
+                            ex[u] = w_exc[j] != 0;
+                            v[u] = n.tgt16[k[u]];
+                            wk[u] = ex[u] ? n.w[k[u]] : n.w_inh;
+                            sk[u] = (ex[u] && stdp) ? n.sd[k[u]] : 0;
+                        }
+                    }
+    #pragma unroll
+                    for (int u = 0; u < kUnroll; ++u) {
+                        if (k[u] < 0) continue;
+                        atomicAdd(&s_in[v[u]], wk[u]);
+                        if (ex[u] && stdp) {
+                            const int32_t a = s_x[v[u]];
+                            if (a) n.sd[k[u]] = sk[u] - a;
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+        for (int sl = 0; sl < kSlots; ++sl) {
+            int32_t *dst = n.I + (size_t)s_col[sl] * npc;
+            const int32_t *in_row = s_in + sl * npc;
+            for (uint32_t loc = threadIdx.x; loc < npc; loc += blockDim.x) {
+                const int32_t x = in_row[loc];
+                if (x) red_add(&dst[loc], x);
+            }
+        }
+        if (threadIdx.x == 0) s_unit = gridDim.x + atomicAdd(&n.ctr->staged_cursor, 1u);
+        __syncthreads();
+        col = s_unit;
     }
     if (lane != 0) ev_all = ev_exc = 0;
     const unsigned long long ba = block_sum(ev_all);
@@ -462,115 +612,124 @@ __global__ void __launch_bounds__(1024) k_dense(DevNet n, const int *t_now)
     const bool ltp_on = owed && stdp;
     const bool deriv_on = owed && n.deriv_period && (t % (int)n.deriv_period) == 0;
     const uint32_t chunks = (npc + n.dense_rows - 1) / n.dense_rows;
-    const uint32_t col = blockIdx.x / chunks;
-    const uint32_t r0 = (blockIdx.x - col * chunks) * n.dense_rows;
-    const uint32_t r1 = min(npc, r0 + n.dense_rows);
-
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x < kSlots) s_col[threadIdx.x] = (uint32_t)n.nbr[col * kSlotStride + threadIdx.x];
     for (int i = threadIdx.x; i < kLut; i += blockDim.x) {
         s_lutp[i] = n.lut_p[i];
         s_lutm[i] = n.lut_m[i];
     }
-    __syncthreads();
-    for (int sl = 0; sl < kSlots; ++sl) {
-        const int32_t *ls = n.last_spike + (size_t)s_col[sl] * npc;
-        uint16_t *x_row = s_x + sl * npc;
-        int32_t *in_row = s_in + sl * npc;
-        for (uint32_t loc = threadIdx.x; loc < npc; loc += blockDim.x) {
-            const int lag = min(t - ls[loc], 255);
-            x_row[loc] = (uint16_t)((lag == 1 ? kFiredLast : 0u) | (stdp ? (uint32_t)s_lutm[lag] : 0u));
-            in_row[loc] = 0;
-        }
-    }
-    __syncthreads();
     drive(n, t, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
-
     int32_t *w_off = s_off + warp * 32;
     int32_t *w_amt = s_amt + warp * 32;
     const int D = (int)n.D;
     const uint32_t dmask = (2u << D) - 2u;            // buckets 1..D
     unsigned long long ev_all = 0, ev_exc = 0;
-    // row metadata goes out one row ahead: the spike-history word and, in lane
-    // d <= D, the end of delay bucket d
-    uint2 hv_next = make_uint2(0u, 0u);
-    int off_next = 0;
-    if (r0 + warp < r1) {
-        const uint32_t p = col * npc + r0 + warp;
-        hv_next = n.hl[p];
-        off_next = (lane <= D) ? (int)n.doff[(size_t)p * kDoffStride + lane] : 0;
-    }
-    for (uint32_t r = r0 + warp; r < r1; r += nwarps) {
-        const uint32_t p = col * npc + r;
-        const bool exc = r < n.ne;
-        const uint2 hv = hv_next;
-        const int hi = off_next;
-        if (r + nwarps < r1) {
-            hv_next = n.hl[p + nwarps];
-            off_next = (lane <= D) ? (int)n.doff[(size_t)(p + nwarps) * kDoffStride + lane] : 0;
-        }
-        const uint32_t h = hv.x;                      // bit k: fired at t - 1 - k
-        const uint32_t fbits = deliver_on ? (h << 1) & dmask : 0u;
-        const int lo = __shfl_up_sync(0xffffffffu, hi, 1);
-        const int m = __shfl_sync(0xffffffffu, hi, D);
-        // lane d (1..D) prepares bucket d
-        int len = 0;
-        int32_t amt = 0;
-        if (lane == 0) w_off[0] = 0;
-        if (lane >= 1 && lane <= D) {
-            len = hi - lo;
-            w_off[lane] = hi;
-            if (exc && ltp_on && len) {
-                const uint32_t recent = h & (0xffffffffu << lane);
-                const int lag = recent ? (__ffs(recent) - 1 - lane) : (t - 1 - (int)hv.y - lane);
-                amt = lag < kLut ? s_lutp[lag] : 0;
+    // the grid is at most one wave of resident blocks; a block takes work
+    // units (a column and a chunk of its rows) from a step-wide cursor
+    __shared__ uint32_t s_unit;
+    for (uint32_t unit = blockIdx.x; unit < n.C * chunks;) {
+        const uint32_t col = unit / chunks;
+        const uint32_t r0 = (unit - col * chunks) * n.dense_rows;
+        const uint32_t r1 = min(npc, r0 + n.dense_rows);
+        if (threadIdx.x < kSlots) s_col[threadIdx.x] = (uint32_t)n.nbr[col * kSlotStride + threadIdx.x];
+        __syncthreads();
+        for (int sl = 0; sl < kSlots; ++sl) {
+            const int32_t *ls = n.last_spike + (size_t)s_col[sl] * npc;
+            uint16_t *x_row = s_x + sl * npc;
+            int32_t *in_row = s_in + sl * npc;
+            for (uint32_t loc = threadIdx.x; loc < npc; loc += blockDim.x) {
+                const int lag = min(t - ls[loc], 255);
+                x_row[loc] = (uint16_t)((lag == 1 ? kFiredLast : 0u) | (stdp ? (uint32_t)s_lutm[lag] : 0u));
+                in_row[loc] = 0;
             }
-            w_amt[lane] = amt;
         }
-        const int delivered = ((fbits >> lane) & 1u) ? len : 0;
-        const bool busy = fbits != 0 || __any_sync(0xffffffffu, amt != 0) || (exc && deriv_on);
-        const int dl = __reduce_add_sync(0xffffffffu, delivered);
-        if (lane == 0) {
-            ev_all += (unsigned long long)dl;
-            if (exc) ev_exc += (unsigned long long)dl;
+        __syncthreads();
+        // row metadata goes out one row ahead: the spike-history word and, in lane
+        // d <= D, the end of delay bucket d
+        uint2 hv_next = make_uint2(0u, 0u);
+        int off_next = 0;
+        if (r0 + warp < r1) {
+            const uint32_t p = col * npc + r0 + warp;
+            hv_next = n.hl[p];
+            off_next = (lane <= D) ? (int)n.doff[(size_t)p * kDoffStride + lane] : 0;
         }
-        __syncwarp();
-        if (!exc && n.D_inh == 1) {
-            // inhibitory row of a generated net: one bucket (delay 1), one
-            // weight, nothing plastic
-            if (fbits & 2u) {
-                const uint4 *rt4 = reinterpret_cast<const uint4 *>(n.tgt16 + row_base(n, p));
-                for (int c = lane; c * 8 < m; c += 32) {
-                    const uint4 tv = rt4[c];
-                    const int nv = min(8, m - c * 8);
-                    const uint32_t tw[4] = {tv.x, tv.y, tv.z, tv.w};
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        const uint32_t v = (u & 1) ? (tw[u >> 1] >> 16) : (tw[u >> 1] & 0xffffu);
-                        if (u < nv) atomicAdd(&s_in[v], n.w_inh);
+        for (uint32_t r = r0 + warp; r < r1; r += nwarps) {
+            const uint32_t p = col * npc + r;
+            const bool exc = r < n.ne;
+            const uint2 hv = hv_next;
+            const int hi = off_next;
+            if (r + nwarps < r1) {
+                hv_next = n.hl[p + nwarps];
+                off_next = (lane <= D) ? (int)n.doff[(size_t)(p + nwarps) * kDoffStride + lane] : 0;
+            }
+            const uint32_t h = hv.x;                      // bit k: fired at t - 1 - k
+            const uint32_t fbits = deliver_on ? (h << 1) & dmask : 0u;
+            const int lo = __shfl_up_sync(0xffffffffu, hi, 1);
+            const int m = __shfl_sync(0xffffffffu, hi, D);
+            // lane d (1..D) prepares bucket d
+            int len = 0;
+            int32_t amt = 0;
+            if (lane == 0) w_off[0] = 0;
+            if (lane >= 1 && lane <= D) {
+                len = hi - lo;
+                w_off[lane] = hi;
+                if (exc && ltp_on && len) {
+                    const uint32_t recent = h & (0xffffffffu << lane);
+                    const int lag = recent ? (__ffs(recent) - 1 - lane) : (t - 1 - (int)hv.y - lane);
+                    amt = lag < kLut ? s_lutp[lag] : 0;
+                }
+                w_amt[lane] = amt;
+            }
+            const int delivered = ((fbits >> lane) & 1u) ? len : 0;
+            const bool busy = fbits != 0 || __any_sync(0xffffffffu, amt != 0) || (exc && deriv_on);
+            const int dl = __reduce_add_sync(0xffffffffu, delivered);
+            if (lane == 0) {
+                ev_all += (unsigned long long)dl;
+                if (exc) ev_exc += (unsigned long long)dl;
+            }
+            __syncwarp();
+            if (!exc && n.D_inh == 1) {
+                // inhibitory row of a generated net: one bucket (delay 1), one
+                // weight, nothing plastic
+                if (fbits & 2u) {
+                    const uint4 *rt4 = reinterpret_cast<const uint4 *>(n.tgt16 + row_base(n, p));
+                    for (int c = lane; c * 8 < m; c += 32) {
+                        const uint4 tv = rt4[c];
+                        const int nv = min(8, m - c * 8);
+                        const uint32_t tw[4] = {tv.x, tv.y, tv.z, tv.w};
+    #pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            const uint32_t v = (u & 1) ? (tw[u >> 1] >> 16) : (tw[u >> 1] & 0xffffu);
+                            if (u < nv) atomicAdd(&s_in[v], n.w_inh);
+                        }
                     }
                 }
+            } else if (busy) {
+                const float scale = (float)D / (float)m;
+                const int64_t base = row_base(n, p);     // a multiple of 8: rows are padded
+                if (!exc)
+                    dense_row_walk<false, false>(n, base, m, D, scale, fbits, stdp, ltp_on, w_off, w_amt, s_in, s_x,
+                                                 lane);
+                else if (deriv_on)
+                    dense_row_walk<true, true>(n, base, m, D, scale, fbits, stdp, ltp_on, w_off, w_amt, s_in, s_x,
+                                               lane);
+                else
+                    dense_row_walk<true, false>(n, base, m, D, scale, fbits, stdp, ltp_on, w_off, w_amt, s_in, s_x,
+                                                lane);
             }
-        } else if (busy) {
-            const float scale = (float)D / (float)m;
-            const int64_t base = row_base(n, p);     // a multiple of 8: rows are padded
-            if (!exc)
-                dense_row_walk<false, false>(n, base, m, D, scale, fbits, stdp, ltp_on, w_off, w_amt, s_in, s_x, lane);
-            else if (deriv_on)
-                dense_row_walk<true, true>(n, base, m, D, scale, fbits, stdp, ltp_on, w_off, w_amt, s_in, s_x, lane);
-            else
-                dense_row_walk<true, false>(n, base, m, D, scale, fbits, stdp, ltp_on, w_off, w_amt, s_in, s_x, lane);
+            __syncwarp();
         }
-        __syncwarp();
-    }
-    __syncthreads();
-    for (int sl = 0; sl < kSlots; ++sl) {
-        int32_t *dst = n.I + (size_t)s_col[sl] * npc;
-        const int32_t *in_row = s_in + sl * npc;
-        for (uint32_t loc = threadIdx.x; loc < npc; loc += blockDim.x) {
-            const int32_t v = in_row[loc];
-            if (v) red_add(&dst[loc], v);
+        __syncthreads();
+        for (int sl = 0; sl < kSlots; ++sl) {
+            int32_t *dst = n.I + (size_t)s_col[sl] * npc;
+            const int32_t *in_row = s_in + sl * npc;
+            for (uint32_t loc = threadIdx.x; loc < npc; loc += blockDim.x) {
+                const int32_t v = in_row[loc];
+                if (v) red_add(&dst[loc], v);
+            }
         }
+        if (threadIdx.x == 0) s_unit = gridDim.x + atomicAdd(&n.ctr->dense_cursor, 1u);
+        __syncthreads();
+        unit = s_unit;
     }
     if (lane != 0) ev_all = ev_exc = 0;
     const unsigned long long ba = block_sum(ev_all);
@@ -795,6 +954,8 @@ __device__ __forceinline__ void neuron_body(const DevNet &n, const int *t_now, i
     c->step_cnt[par ^ 1][2] = 0;
     c->l_exc_last = c->l_exc - c->l_exc_mark;
     c->l_exc_mark = c->l_exc;
+    c->dense_cursor = 0;
+    c->staged_cursor = 0;
     c->ltp_pending = t;
     c->done_blocks = 0;
     *t_next = t + 1;

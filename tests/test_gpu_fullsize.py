@@ -5,8 +5,9 @@ the launch configuration bench.py times.
 The oracle cannot simulate these sizes, so the checks are (a) outputs the
 oracle computes one by one -- sampled rows of the generated network and
 sampled thalamic draws -- and (b) properties that hold at any size: the same
-run through the dense/automatic path and through the event-driven path only
-(a different launch shape) gives bit-identical rasters, weights and counters,
+run through the dense/automatic path and through each event-driven delivery
+only (global reductions; column by column through shared memory) gives
+bit-identical rasters, weights and counters,
 the raster is sorted, unique and in range, and the counters agree with it.
 """
 import hashlib
@@ -85,8 +86,11 @@ def test_full_size_structure_paths_and_invariants(eng, orc, name):
     assert np.all(np.diff(key) > 0) and g.min() >= 0 and g.max() < n and t.max() < STEPS
     assert 0 < c_auto["e_exc"] <= c_auto["e_all"] and c_auto["error"] == 0
 
-    # (b) the event-driven path alone gives the identical run
-    _, _, digest_sparse, c_sparse = _run(eng, cfg, dict(dense_permille=1001, graph_steps=1), sources)
-    assert digest_sparse == digest_auto
-    for k in ("spikes", "e_all", "e_exc", "l_exc"):
-        assert c_sparse[k] == c_auto[k], k
+    # (b) the event-driven path alone, with global reductions or column by
+    # column through shared memory, gives the identical run
+    for shape in (dict(dense_permille=1001, staged_permille=0xffffffff, graph_steps=1),
+                  dict(dense_permille=1001, staged_permille=1)):
+        _, _, digest_sparse, c_sparse = _run(eng, cfg, shape, sources)
+        assert digest_sparse == digest_auto, shape
+        for k in ("spikes", "e_all", "e_exc", "l_exc"):
+            assert c_sparse[k] == c_auto[k], (shape, k)

@@ -22,16 +22,21 @@ def eng():
     return e
 
 
-MODES = {"auto": None, "sparse": 1001, "dense": 1}
+MODES = {"auto": None,
+         "sparse": dict(dense_permille=1001, staged_permille=0xffffffff),
+         "staged": dict(dense_permille=1001, staged_permille=1),
+         "dense": dict(dense_permille=1)}
 
 
 def gpu_net(eng, cfg, mode="auto", **kw):
     """mode: 'auto' (device picks per step), 'sparse' (event-driven kernels
-    only) or 'dense' (the dense synapse pass whenever any neuron fired)."""
+    with global reductions only), 'staged' (event-driven delivery column by
+    column through shared memory whenever anything is due) or 'dense' (the
+    dense synapse pass whenever any neuron fired)."""
     kw.setdefault("raster_capacity", 1 << 22)
     n = eng.Network(cfg, **kw)
     if MODES[mode] is not None:
-        n.set_launch(dense_permille=MODES[mode])
+        n.set_launch(**MODES[mode])
     return n
 
 
@@ -79,7 +84,7 @@ def test_generated_network_equals_oracle(eng, orc, cfg):
 # ---------------------------------------------------------------------------
 # whole runs, bit-exact
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("mode", ["auto", "sparse", "dense"])
+@pytest.mark.parametrize("mode", ["auto", "sparse", "staged", "dense"])
 def test_col1_m100_full_second_bitexact(eng, orc, mode):
     cfg = workloads.workload("col1_m100")
     o = orc.Oracle(cfg)
@@ -92,7 +97,7 @@ def test_col1_m100_full_second_bitexact(eng, orc, mode):
             assert n.profile()["dense_steps"] > 300
 
 
-@pytest.mark.parametrize("mode", ["auto", "sparse", "dense"])
+@pytest.mark.parametrize("mode", ["auto", "sparse", "staged", "dense"])
 @pytest.mark.parametrize("gx,gy,m,T,seed", [
     (2, 2, 60, 1100, 31),        # ring members coincide on a 2x2 torus; crosses a derivative update
     (3, 3, 100, 1050, 32),
@@ -118,7 +123,7 @@ def grid8_onset(orc):
     return o
 
 
-@pytest.mark.parametrize("mode", ["auto", "sparse", "dense"])
+@pytest.mark.parametrize("mode", ["auto", "sparse", "staged", "dense"])
 def test_grid8_m1125_onset_bitexact(eng, grid8_onset, mode):
     with gpu_net(eng, workloads.workload("grid8_m1125"), mode) as n:
         n.run(32)
@@ -126,7 +131,7 @@ def test_grid8_m1125_onset_bitexact(eng, grid8_onset, mode):
         assert n.counters()["spikes"] > 100000
 
 
-@pytest.mark.parametrize("mode", ["sparse", "dense"])
+@pytest.mark.parametrize("mode", ["sparse", "staged", "dense"])
 @pytest.mark.parametrize("flag_pair", [("STDP_OFF", 1, 1), ("DELIVERY_OFF", 2, 2)])
 def test_debug_flags_bitexact(eng, orc, flag_pair, mode):
     _, of, gf = flag_pair
@@ -202,6 +207,8 @@ SHAPES = [
          graph_steps=20, deriv_block=64, dense_permille=1, dense_block=128, dense_rows=37),
     dict(graph_steps=10, dense_permille=1, dense_block=512, dense_rows=1250),
     dict(graph_steps=2, dense_permille=20, dense_block=32, dense_rows=1),
+    dict(graph_steps=4, dense_permille=1001, staged_permille=1),
+    dict(graph_steps=1, dense_permille=200, staged_permille=300, deliver_block=128),
 ]
 
 
@@ -234,7 +241,7 @@ def test_step_by_step_equals_run(eng):
 # ---------------------------------------------------------------------------
 # checkpoint / resume, host end-to-end call
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("mode", ["auto", "dense"])
+@pytest.mark.parametrize("mode", ["auto", "staged", "dense"])
 def test_checkpoint_resume_is_bitexact(eng, mode):
     cfg = workloads.custom(grid_x=2, grid_y=2, fanout=100, pct_ring=(40, 30, 20, 10), seed=61)
     with gpu_net(eng, cfg, mode) as a:
