@@ -540,7 +540,7 @@ int start_net(const snn_config *cfg, void *cuda_stream, size_t budget, snn_net *
     net->launch.graph_steps = 50;
     net->launch.dense_block = 512;
     net->launch.dense_rows = 0;
-    net->launch.dense_permille = 50;
+    net->launch.dense_permille = 250;
     net->launch.staged_permille = 10000;
     (void)cuda_stream;
     return SNN_OK;
