@@ -407,7 +407,7 @@ int setup_dense(snn_net *net)
         SNN_CUDA(cudaFuncSetAttribute(k_deliver_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sbytes));
         int per_sm = 0;
         SNN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_deliver_cols, (int)kStagedBlock, sbytes));
-        if (per_sm >= 1) {
+        if (per_sm >= 1 && net->launch.staged_permille != 0xffffffffu) {
             net->dn.staged_ok = 1;
             net->staged_grid = (int)std::min<int64_t>(net->dn.C, (int64_t)per_sm * net->sm_count);
             const uint32_t pm = net->launch.staged_permille;
@@ -541,7 +541,9 @@ int start_net(const snn_config *cfg, void *cuda_stream, size_t budget, snn_net *
     net->launch.dense_block = 512;
     net->launch.dense_rows = 0;
     net->launch.dense_permille = 250;
-    net->launch.staged_permille = 10000;
+    // column staging pays from about 10 events per neuron and step on nets of
+    // distinct neighbour columns; smaller tori default to never (no launch)
+    net->launch.staged_permille = cfg->grid_x * cfg->grid_y >= 16 ? 10000u : 0xffffffffu;
     (void)cuda_stream;
     return SNN_OK;
 }
