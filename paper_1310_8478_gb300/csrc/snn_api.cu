@@ -111,6 +111,7 @@ struct snn_net {
     bool dense_ok = false;          // the dense pass can run on this net
     int dense_grid = 0;             // blocks of the dense pass (at most one wave of resident blocks)
     int staged_grid = 0;            // blocks of the column-staged delivery (likewise)
+    int ordered_grid = 0;           // blocks of the column-ordered delivery (likewise)
     uint64_t version = 0;           // bumped whenever captured launches go stale
     // stimulus
     size_t stim_cap = 0;
@@ -394,7 +395,17 @@ int setup_dense(snn_net *net)
     net->dense_ok = false;
     net->dn.staged_ok = 0;
     net->dn.staged_min_events = ~0ull;
-    if (!net->tgt16 || net->cfg.neurons_per_col > kDenseMaxNpc) return SNN_OK;
+    net->dn.ordered_ok = 0;
+    if (!net->tgt16) return SNN_OK;
+    {
+        int per_sm = 0;
+        SNN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_deliver_ordered, (int)kOrderedBlock, 0));
+        if (per_sm >= 1) {
+            net->dn.ordered_ok = 1;
+            net->ordered_grid = (int)std::min<int64_t>(net->dn.C, (int64_t)per_sm * net->sm_count);
+        }
+    }
+    if (net->cfg.neurons_per_col > kDenseMaxNpc) return SNN_OK;
     // both stage each depression amount in 15 bits
     std::vector<int32_t> lut;
     if (build_luts(&net->cfg, lut) != SNN_OK) return SNN_OK;
@@ -639,7 +650,8 @@ void launch_step(snn_net *net, int32_t t, cudaStream_t s)
         mark(3);
     }
     mark(0);
-    k_deliver<<<g_del, L.deliver_block, 0, s>>>(dn, t_now);
+    if (dn.ordered_ok) k_deliver_ordered<<<net->ordered_grid, kOrderedBlock, 0, s>>>(dn, t_now);
+    else k_deliver<<<g_del, L.deliver_block, 0, s>>>(dn, t_now);
     if (dn.staged_ok)
         k_deliver_cols<<<net->staged_grid, kStagedBlock, staged_smem_bytes(dn.npc, kStagedBlock), s>>>(dn, t_now);
     mark(0);

@@ -46,6 +46,7 @@ struct DevNet {
     uint32_t N, npc, ne, C, D;       // neurons, per column, excitatory per column, columns, max delay
     uint32_t D_inh;                  // largest delay of an inhibitory synapse (1 for generated nets)
     int staged_ok;                   // the column-staged delivery may run (compact targets, staging fits)
+    int ordered_ok;                  // the column-ordered delivery replaces the ring-order one (compact targets)
     unsigned long long staged_min_events;   // it runs when a step's expected events reach this
     int32_t w_inh;                   // generated nets: the weight of every inhibitory synapse (not
                                      //                 plastic); the dense pass reads no inhibitory w
@@ -243,6 +244,13 @@ __device__ __forceinline__ bool staged_selected(const DevNet &n, int t)
     return est >= n.staged_min_events;
 }
 
+// compact nets deliver the remaining event-driven steps column by column with
+// global reductions
+__device__ __forceinline__ bool ordered_selected(const DevNet &n, int t)
+{
+    return n.ordered_ok && !dense_selected(n, t) && !staged_selected(n, t);
+}
+
 __device__ __forceinline__ int64_t row_base(const DevNet &n, uint32_t p)
 {
     return n.uniform_m ? (int64_t)p * n.uniform_m : n.row_off[p];
@@ -284,6 +292,7 @@ __global__ void k_read_rows(DevNet n, GenParams g, const uint8_t *canon_delay, u
 __global__ void k_deliver(DevNet n, const int *t_now);
 __global__ void k_dense(DevNet n, const int *t_now);
 __global__ void k_deliver_cols(DevNet n, const int *t_now);
+__global__ void k_deliver_ordered(DevNet n, const int *t_now);
 __global__ void k_neuron_f32(DevNet n, const int *t_now, int *t_next);
 __global__ void k_neuron_f64(DevNet n, const int *t_now, int *t_next);
 __global__ void k_probe(DevNet n, const int *t_now);
@@ -294,5 +303,6 @@ __global__ void k_fold(DevNet n, const int *t_now, int force);
 size_t dense_smem_bytes(uint32_t npc, uint32_t block);
 size_t staged_smem_bytes(uint32_t npc, uint32_t block);
 constexpr uint32_t kStagedBlock = 512;      // threads per block of the column-staged delivery
+constexpr uint32_t kOrderedBlock = 256;     // threads per block of the column-ordered delivery
 
 }  // namespace snn

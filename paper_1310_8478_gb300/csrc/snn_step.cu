@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(1024) k_deliver(DevNet n, const int *t_now)
     __shared__ int s_tile_start[32 * 33];        // per warp: prefix of the items' lengths
     __shared__ uint32_t s_tile_info[32 * 32];    // per warp: kind and source column of each item
     const int t = *t_now;
-    if (dense_selected(n, t) || staged_selected(n, t)) return;
+    if (dense_selected(n, t) || staged_selected(n, t) || n.ordered_ok) return;
     const bool stdp = !(n.flags & SNN_STDP_OFF);
     const int nl = (int)(n.D + n.D_inh);
     for (int i = threadIdx.x; i < kLut; i += blockDim.x) s_lut[i] = n.lut_m[i];
@@ -214,15 +214,20 @@ __global__ void __launch_bounds__(1024) k_deliver(DevNet n, const int *t_now)
 }
 
 // ---------------------------------------------------------------------------
-// sparse S1, column by column (generated nets with compact targets, in steps
-// with many events): block per source column.  The 13 columns its synapses
-// reach are staged in shared memory -- the input accumulator and the LTD
-// amount at each neuron's current lag -- so that an event costs a shared
-// atomic and a shared load instead of a random L2 reduction and a random
-// gather.  A warp scans 32 rows at a time, turns every delay bucket d whose
-// source fired at t - d into an item, and walks the concatenated synapses of
-// 32 items with all lanes; the input is flushed with one coalesced reduction
-// per touched neuron.
+// sparse S1, column by column (generated nets with compact targets).  A
+// persistent grid takes source columns from a step-wide cursor, so the
+// columns in flight form a narrow band of the torus and so do the targets
+// they reach.  A warp scans 32 rows of the column at a time, turns every
+// delay bucket d whose source fired at t - d into an item, and walks the
+// concatenated synapses of 32 items with all lanes.
+//   kStage (steps with many events): the input accumulators and LTD amounts
+//   of the 13 columns the block's synapses reach are staged in shared memory,
+//   so an event costs a shared atomic and a shared load; the input is flushed
+//   with one coalesced reduction per touched neuron.
+//   otherwise: an event is an L2 reduction into the target's input and a
+//   gather of its last spike, both on the band of columns in flight, which
+//   stays in L2 (the ring-list order of k_deliver sweeps the whole torus once
+//   per delay instead).
 // ---------------------------------------------------------------------------
 constexpr int kTileWords = 32 + 33 + 32;     // per warp: item starts, length prefix, kinds
 
@@ -232,18 +237,14 @@ size_t staged_smem_bytes(uint32_t npc, uint32_t block)
            (((size_t)kSlots * npc * 2 + 15) & ~size_t(15));
 }
 
-__global__ void __launch_bounds__(kStagedBlock) k_deliver_cols(DevNet n, const int *t_now)
+template <bool kStage>
+__device__ __forceinline__ void deliver_cols(const DevNet &n, int t, int32_t *s_lut, int32_t *s_in, int32_t *s_tile,
+                                             uint16_t *s_x)
 {
-    extern __shared__ int4 smem_i4[];
     __shared__ uint32_t s_col[kSlots];
-    const int t = *t_now;
-    if (!staged_selected(n, t)) return;
+    __shared__ uint32_t s_unit;
     const uint32_t npc = n.npc;
     const uint32_t nwarps = blockDim.x >> 5;
-    int32_t *s_lut = reinterpret_cast<int32_t *>(smem_i4);
-    int32_t *s_in = s_lut + kLut;                                        // [kSlots * npc]
-    int32_t *s_tile = s_in + kSlots * npc;                               // [nwarps][kTileWords]
-    uint16_t *s_x = reinterpret_cast<uint16_t *>(s_tile + nwarps * kTileWords);   // [kSlots * npc]
     const bool stdp = !(n.flags & SNN_STDP_OFF);
     const bool deliver_on = !(n.flags & SNN_DELIVERY_OFF);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -255,24 +256,23 @@ __global__ void __launch_bounds__(kStagedBlock) k_deliver_cols(DevNet n, const i
     int32_t *w_start = w_lo + 32;                              // [33] prefix of the lengths
     int32_t *w_exc = w_start + 33;                             // [32] 1: excitatory row
     unsigned long long ev_all = 0, ev_exc = 0;
-    // the grid is at most one wave of resident blocks; a block takes columns
-    // from a step-wide cursor
-    __shared__ uint32_t s_unit;
     for (uint32_t col = blockIdx.x; col < n.C;) {
         if (threadIdx.x < kSlots) s_col[threadIdx.x] = (uint32_t)n.nbr[col * kSlotStride + threadIdx.x];
         __syncthreads();
-        // the LTD amount (at most 15 bits: the host checks the table) of every
-        // staged neuron at its lag t - last_spike >= 1, saturated at the table end
-        for (int sl = 0; sl < kSlots; ++sl) {
-            const int32_t *ls = n.last_spike + (size_t)s_col[sl] * npc;
-            uint16_t *x_row = s_x + sl * npc;
-            int32_t *in_row = s_in + sl * npc;
-            for (uint32_t loc = threadIdx.x; loc < npc; loc += blockDim.x) {
-                x_row[loc] = stdp ? (uint16_t)s_lut[min(t - ls[loc], kLut - 1)] : (uint16_t)0;
-                in_row[loc] = 0;
+        if (kStage) {
+            // the LTD amount (at most 15 bits: the host checks the table) of every
+            // staged neuron at its lag t - last_spike >= 1, saturated at the table end
+            for (int sl = 0; sl < kSlots; ++sl) {
+                const int32_t *ls = n.last_spike + (size_t)s_col[sl] * npc;
+                uint16_t *x_row = s_x + sl * npc;
+                int32_t *in_row = s_in + sl * npc;
+                for (uint32_t loc = threadIdx.x; loc < npc; loc += blockDim.x) {
+                    x_row[loc] = stdp ? (uint16_t)s_lut[min(t - ls[loc], kLut - 1)] : (uint16_t)0;
+                    in_row[loc] = 0;
+                }
             }
+            __syncthreads();
         }
-        __syncthreads();
         const int64_t cbase = (int64_t)col * npc * n.uniform_m;   // first synapse of the column
         for (uint32_t rb = warp * 32; rb < npc; rb += nwarps * 32) {
             const uint32_t r = rb + lane;
@@ -291,7 +291,7 @@ __global__ void __launch_bounds__(kStagedBlock) k_deliver_cols(DevNet n, const i
                     exc = r < n.ne ? 1 : 0;
                 }
                 int incl = len;
-    #pragma unroll
+#pragma unroll
                 for (int o = 1; o < 32; o <<= 1) {
                     const int y = __shfl_up_sync(0xffffffffu, incl, o);
                     if (lane >= o) incl += y;
@@ -308,14 +308,14 @@ __global__ void __launch_bounds__(kStagedBlock) k_deliver_cols(DevNet n, const i
                 }
                 __syncwarp();
                 // kUnroll synapses per lane in flight: targets, weights and
-                // derivatives first, then the staged updates
+                // derivatives first, then the updates
                 int j = 0;
                 for (int e0 = lane; e0 < tile_len; e0 += 32 * kUnroll) {
                     int64_t k[kUnroll];
                     uint32_t v[kUnroll];
-                    int32_t wk[kUnroll], sk[kUnroll];
+                    int32_t wk[kUnroll], sk[kUnroll], ls[kUnroll];
                     bool ex[kUnroll];
-    #pragma unroll
+#pragma unroll
                     for (int u = 0; u < kUnroll; ++u) {
                         const int e = e0 + 32 * u;
                         k[u] = -1;
@@ -328,13 +328,33 @@ __global__ void __launch_bounds__(kStagedBlock) k_deliver_cols(DevNet n, const i
                             sk[u] = (ex[u] && stdp) ? n.sd[k[u]] : 0;
                         }
                     }
-    #pragma unroll
-                    for (int u = 0; u < kUnroll; ++u) {
-                        if (k[u] < 0) continue;
-                        atomicAdd(&s_in[v[u]], wk[u]);
-                        if (ex[u] && stdp) {
-                            const int32_t a = s_x[v[u]];
-                            if (a) n.sd[k[u]] = sk[u] - a;
+                    if (kStage) {
+#pragma unroll
+                        for (int u = 0; u < kUnroll; ++u) {
+                            if (k[u] < 0) continue;
+                            atomicAdd(&s_in[v[u]], wk[u]);
+                            if (ex[u] && stdp) {
+                                const int32_t a = s_x[v[u]];
+                                if (a) n.sd[k[u]] = sk[u] - a;
+                            }
+                        }
+                    } else {
+#pragma unroll
+                        for (int u = 0; u < kUnroll; ++u) {
+                            if (k[u] < 0) continue;
+                            const uint32_t slot = __umulhi(v[u], n.npc_recip);
+                            v[u] = s_col[slot] * npc + (v[u] - slot * npc);      // target gid
+                            red_add(&n.I[v[u]], wk[u]);
+                            ls[u] = (ex[u] && stdp) ? n.last_spike[v[u]] : 0;
+                        }
+#pragma unroll
+                        for (int u = 0; u < kUnroll; ++u) {
+                            if (k[u] < 0 || !(ex[u] && stdp)) continue;
+                            const int lag = t - ls[u];                         // >= 1
+                            if (lag < kLut) {
+                                const int32_t a = s_lut[lag];
+                                if (a) n.sd[k[u]] = sk[u] - a;
+                            }
                         }
                     }
                 }
@@ -342,12 +362,14 @@ __global__ void __launch_bounds__(kStagedBlock) k_deliver_cols(DevNet n, const i
             }
         }
         __syncthreads();
-        for (int sl = 0; sl < kSlots; ++sl) {
-            int32_t *dst = n.I + (size_t)s_col[sl] * npc;
-            const int32_t *in_row = s_in + sl * npc;
-            for (uint32_t loc = threadIdx.x; loc < npc; loc += blockDim.x) {
-                const int32_t x = in_row[loc];
-                if (x) red_add(&dst[loc], x);
+        if (kStage) {
+            for (int sl = 0; sl < kSlots; ++sl) {
+                int32_t *dst = n.I + (size_t)s_col[sl] * npc;
+                const int32_t *in_row = s_in + sl * npc;
+                for (uint32_t loc = threadIdx.x; loc < npc; loc += blockDim.x) {
+                    const int32_t x = in_row[loc];
+                    if (x) red_add(&dst[loc], x);
+                }
             }
         }
         if (threadIdx.x == 0) s_unit = gridDim.x + atomicAdd(&n.ctr->staged_cursor, 1u);
@@ -361,6 +383,28 @@ __global__ void __launch_bounds__(kStagedBlock) k_deliver_cols(DevNet n, const i
         atomicAdd(&n.ctr->e_all, ba);
         atomicAdd(&n.ctr->e_exc, be);
     }
+}
+
+__global__ void __launch_bounds__(kStagedBlock) k_deliver_cols(DevNet n, const int *t_now)
+{
+    extern __shared__ int4 smem_i4[];
+    const int t = *t_now;
+    if (!staged_selected(n, t)) return;
+    const uint32_t npc = n.npc, nwarps = blockDim.x >> 5;
+    int32_t *s_lut = reinterpret_cast<int32_t *>(smem_i4);
+    int32_t *s_in = s_lut + kLut;                                        // [kSlots * npc]
+    int32_t *s_tile = s_in + kSlots * npc;                               // [nwarps][kTileWords]
+    uint16_t *s_x = reinterpret_cast<uint16_t *>(s_tile + nwarps * kTileWords);   // [kSlots * npc]
+    deliver_cols<true>(n, t, s_lut, s_in, s_tile, s_x);
+}
+
+__global__ void __launch_bounds__(kOrderedBlock) k_deliver_ordered(DevNet n, const int *t_now)
+{
+    __shared__ int32_t s_lut[kLut];
+    __shared__ int32_t s_tile[(kOrderedBlock / 32) * kTileWords];
+    const int t = *t_now;
+    if (!ordered_selected(n, t)) return;
+    deliver_cols<false>(n, t, s_lut, nullptr, s_tile, nullptr);
 }
 
 // ---------------------------------------------------------------------------

@@ -114,6 +114,19 @@ def test_small_grids_bitexact_across_derivative_updates(eng, orc, gx, gy, m, T, 
         assert_same_run(o, n)
 
 
+def test_big_columns_with_32_bit_targets_bitexact(eng, orc):
+    # columns above 4096 neurons keep 32-bit target ids: the ring-order
+    # event-driven delivery (no column passes) against the oracle
+    cfg = workloads.custom(grid_x=2, grid_y=1, neurons_per_col=4200, exc_per_col=3360, fanout=24,
+                           pct_ring=(40, 30, 20, 10), seed=35, w_exc0_q16=12 * 65536)
+    o = orc.Oracle(cfg)
+    o.run(300)
+    with gpu_net(eng, cfg) as n:
+        n.run(300)
+        assert_same_run(o, n)
+        assert n.counters()["spikes"] > 100
+
+
 @pytest.fixture(scope="module")
 def grid8_onset(orc):
     # the 8x8, M = 1125 workload over its first 32 ms: activity grows from the
