@@ -128,7 +128,7 @@ typedef struct {
                                         the last max_delay steps x fan-out / max_delay, plus
                                         inhibitory spikes of the step before x fan-out) reach this
                                         many per 1000 neurons; 0xffffffff = never (the default
-                                        for nets of fewer than 16 columns, else 10000) */
+                                        for nets of fewer than 16 columns, else 30000) */
 } snn_launch;
 
 /* Per-kernel device time collected while profiling is on (CUDA events), and

@@ -552,9 +552,9 @@ int start_net(const snn_config *cfg, void *cuda_stream, size_t budget, snn_net *
     net->launch.dense_block = 512;
     net->launch.dense_rows = 0;
     net->launch.dense_permille = 250;
-    // column staging pays from about 10 events per neuron and step on nets of
+    // column staging pays from about 30 events per neuron and step on nets of
     // distinct neighbour columns; smaller tori default to never (no launch)
-    net->launch.staged_permille = cfg->grid_x * cfg->grid_y >= 16 ? 10000u : 0xffffffffu;
+    net->launch.staged_permille = cfg->grid_x * cfg->grid_y >= 16 ? 30000u : 0xffffffffu;
     (void)cuda_stream;
     return SNN_OK;
 }
