@@ -612,6 +612,7 @@ void launch_flush(snn_net *net)
     const int *t_now = &net->ctr->t_slot[t & 1];
     k_ltp<<<grid_for(net, net->launch.ltp_blocks_per_sm), net->launch.ltp_block, 0, s>>>(dn, t_now, 1);
     k_fold<<<sized_grid(net, 8, net->n_rin, 4096), 256, 0, s>>>(dn, t_now, 1);
+    cudaMemsetAsync(&net->ctr->fold_cursor, 0, sizeof(unsigned), s);      // no step closes after this fold
     const uint32_t P = net->cfg.deriv_period_ms;
     if (P && t > 0 && (uint32_t)t % P == 0)
         k_deriv<<<sized_grid(net, 8, (int64_t)dn.C * dn.ne, net->launch.deriv_block / 32), net->launch.deriv_block, 0,
@@ -1790,6 +1791,7 @@ int snn_load_state(snn_net *net, const void *host_buf, size_t n)
     hc.done_blocks = 0;
     hc.dense_cursor = 0;
     hc.staged_cursor = 0;
+    hc.fold_cursor = 0;
     SNN_CUDA(cudaMemcpyAsync(net->ctr, &hc, sizeof hc, cudaMemcpyHostToDevice, s));
     if (dn.raster_step_off) SNN_CUDA(cudaMemsetAsync(dn.raster_step_off, 0, 8, s));
     SNN_CUDA(cudaStreamSynchronize(s));

@@ -39,6 +39,7 @@ struct DevCounters {
     unsigned long long l_exc_last;   // excitatory in-degree of the neurons that fired in the last step
     unsigned dense_cursor;           // work units of the dense pass handed out in this step
     unsigned staged_cursor;          // columns of the column-staged delivery handed out in this step
+    unsigned fold_cursor;            // chunks of reverse entries handed out by the current fold
 };
 
 // Everything a step kernel needs, passed by value.

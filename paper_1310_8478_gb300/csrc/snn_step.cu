@@ -471,13 +471,36 @@ __global__ void __launch_bounds__(1024) k_fold(DevNet n, const int *t_now, int f
         const int t = *t_now;        // only before a long-term update (t closes a period)
         if (!n.deriv_period || t <= 0 || (t % (int)n.deriv_period) != 0) return;
     }
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n.n_rin; e += stride) {
-        const int32_t v = n.sd_rev[e];
-        if (!v) continue;
-        const uint64_t r = n.rin[e];
-        n.sd[row_base(n, (uint32_t)r) + ((uint32_t)(r >> 32) & 0xffffu)] += v;
-        n.sd_rev[e] = 0;
+    // Chunks of consecutive reverse entries (targets in order) are handed out
+    // in order, so the targets in flight form a narrow band of the torus and
+    // so do the source rows their synapses scatter into: the scatter stays in
+    // L2.  Four entries per thread in flight.
+    __shared__ int64_t s_chunk;
+    constexpr int64_t kChunk = 8192;
+    for (int64_t c0 = (int64_t)blockIdx.x * kChunk; c0 < n.n_rin;) {
+        const int64_t c1 = min(c0 + kChunk, n.n_rin);
+        for (int64_t e0 = c0 + threadIdx.x; e0 < c1; e0 += 4 * (int64_t)blockDim.x) {
+            int32_t v[4];
+            uint64_t r[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t e = e0 + u * (int64_t)blockDim.x;
+                v[u] = e < c1 ? n.sd_rev[e] : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (v[u]) r[u] = n.rin[e0 + u * (int64_t)blockDim.x];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (!v[u]) continue;
+                n.sd[row_base(n, (uint32_t)r[u]) + ((uint32_t)(r[u] >> 32) & 0xffffu)] += v[u];
+                n.sd_rev[e0 + u * (int64_t)blockDim.x] = 0;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) s_chunk = (int64_t)(gridDim.x + atomicAdd(&n.ctr->fold_cursor, 1u)) * kChunk;
+        __syncthreads();
+        c0 = s_chunk;
     }
 }
 
@@ -1000,6 +1023,7 @@ __device__ __forceinline__ void neuron_body(const DevNet &n, const int *t_now, i
     c->l_exc_mark = c->l_exc;
     c->dense_cursor = 0;
     c->staged_cursor = 0;
+    c->fold_cursor = 0;
     c->ltp_pending = t;
     c->done_blocks = 0;
     *t_next = t + 1;
