@@ -172,11 +172,12 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def kernel_source_digest():
-    """sha256 of the sources the step kernels are compiled from."""
+def kernel_source_digest(kernel: str = "dense"):
+    """sha256 of the sources a step kernel is compiled from (the dense pass
+    has its own file; the other step kernels share snn_step.cu)."""
     import hashlib
     h = hashlib.sha256()
-    for f in ("snn_step.cu", "snn_internal.cuh"):
+    for f in ("snn_dense.cu" if kernel == "dense" else "snn_step.cu", "snn_internal.cuh"):
         with open(os.path.join(ROOT, "paper_1310_8478_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
@@ -189,7 +190,7 @@ def committed_traffic(kernel: str, workload: str):
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
-    if d.get("source_sha256") != kernel_source_digest():
+    if d.get("source_sha256") != kernel_source_digest(kernel):
         return None
     return d.get("dram_bytes_per_launch")
 

@@ -18,7 +18,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(PKG, "_build")
 LIB_PATH = os.path.join(BUILD_DIR, "libsnn.so")
-SOURCES = ["snn_build.cu", "snn_step.cu", "snn_api.cu"]
+SOURCES = ["snn_build.cu", "snn_step.cu", "snn_dense.cu", "snn_api.cu"]
 HEADERS = ["snn_internal.cuh"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -276,6 +276,58 @@ __device__ __forceinline__ unsigned lanemask_lt()
 }
 
 // ---- kernel entry points (defined in snn_build.cu / snn_step.cu) ----------
+// ---------------------------------------------------------------------------
+// device helpers shared by the step kernels
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void red_add(int32_t *p, int32_t v)
+{
+    asm volatile("red.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+template <typename T>
+__device__ __forceinline__ T block_sum(T x)
+{
+    __shared__ T s_part[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) s_part[warp] = x;
+    __syncthreads();
+    T r = 0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r += s_part[i];
+    __syncthreads();
+    return r;   // valid in thread 0
+}
+
+__device__ __forceinline__ int32_t deriv_w(const DevNet &n, int32_t w, int32_t s)
+{
+    long long nw = (long long)w + n.deriv_bias + s;
+    nw = nw < 0 ? 0 : (nw > n.wmax ? n.wmax : nw);
+    return (int32_t)nw;
+}
+
+__device__ __forceinline__ int32_t deriv_sd(const DevNet &n, int32_t s)
+{
+    return (int32_t)(((long long)s * n.deriv_decay + 32768) >> 16);
+}
+
+// thalamic drive (thal_per_col events per column, Philox keyed by (t, col))
+// and the external events of step t, by the threads of a whole grid
+__device__ __forceinline__ void drive(const DevNet &n, int t, uint32_t gtid, uint32_t gthreads)
+{
+    const uint32_t n_thal = n.C * n.thal_per_col;
+    for (uint32_t e = gtid; e < n_thal; e += gthreads) {
+        const uint32_t col = e / n.thal_per_col, k = e - col * n.thal_per_col;
+        const uint4 r = philox10(make_uint4((uint32_t)t, col, 1u, k), n.seed_lo, n.seed_hi);
+        red_add(&n.I[col * n.npc + draw_below(r.x, n.npc)], n.thal_amp);
+    }
+    if (t >= n.stim_t0 && t < n.stim_t1) {
+        const int64_t lo = n.stim_off[t - n.stim_t0], hi = n.stim_off[t - n.stim_t0 + 1];
+        for (int64_t e = lo + gtid; e < hi; e += gthreads) red_add(&n.I[n.stim_gid[e]], n.stim_q16[e]);
+    }
+}
+
 __global__ void k_gen_rows(GenParams g, uint32_t n_rows, uint16_t *doff, int32_t *tgt, uint16_t *tgt16,
                            int32_t *w, int32_t *sd);
 __global__ void k_count_indeg(DevNet n, int32_t *indeg_exc, int32_t *indeg_inh);

@@ -114,6 +114,40 @@ def test_small_grids_bitexact_across_derivative_updates(eng, orc, gx, gy, m, T, 
         assert_same_run(o, n)
 
 
+DEGENERATE = {
+    # no thalamic drive and no stimulus: nothing ever fires, neurons settle
+    "quiet": dict(grid_x=2, grid_y=2, neurons_per_col=100, exc_per_col=80, fanout=60,
+                  pct_ring=(40, 30, 20, 10), seed=36, thal_per_col_per_ms=0),
+    # one synapse per neuron, one delay
+    "m1_d1": dict(grid_x=3, grid_y=3, neurons_per_col=100, exc_per_col=80, fanout=1,
+                  pct_ring=(100, 0, 0, 0), seed=37, max_delay_ms=1, w_exc0_q16=9 * 65536),
+    # the longest delay the layout allows, fan-out not a multiple of 8
+    "d31": dict(grid_x=2, grid_y=2, neurons_per_col=100, exc_per_col=80, fanout=33,
+                pct_ring=(40, 30, 20, 10), seed=38, max_delay_ms=31),
+    # excitatory columns only / a single excitatory neuron per column
+    "all_exc": dict(grid_x=2, grid_y=1, neurons_per_col=50, exc_per_col=50, fanout=40,
+                    pct_ring=(40, 30, 20, 10), seed=39),
+    "one_exc": dict(grid_x=2, grid_y=2, neurons_per_col=20, exc_per_col=1, fanout=15,
+                    pct_ring=(40, 30, 20, 10), seed=40),
+}
+
+
+@pytest.mark.parametrize("mode", ["auto", "sparse", "staged", "dense"])
+@pytest.mark.parametrize("name", sorted(DEGENERATE))
+def test_degenerate_networks_bitexact(eng, orc, name, mode):
+    cfg = workloads.custom(**DEGENERATE[name])
+    o = orc.Oracle(cfg)
+    o.run(1100)                                   # crosses one long-term update
+    with gpu_net(eng, cfg, mode) as n:
+        n.run(1100)
+        assert_same_run(o, n)
+        c = n.counters()
+        if name == "quiet":
+            assert c["spikes"] == 0 and c["e_all"] == 0
+        else:
+            assert c["spikes"] > 0
+
+
 def test_big_columns_with_32_bit_targets_bitexact(eng, orc):
     # columns above 4096 neurons keep 32-bit target ids: the ring-order
     # event-driven delivery (no column passes) against the oracle
