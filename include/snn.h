@@ -50,6 +50,8 @@ extern "C" {
 #define SNN_ETIMEOUT (-5)   /* a bounded device-side wait gave up */
 #define SNN_ETRUNC (-6)     /* output buffer too small; *n_out holds the size needed */
 #define SNN_ESTATE (-7)     /* the call does not fit the handle's state */
+#define SNN_EBOUNDS (-8)    /* checked build (-DSNN_CHECKED): a kernel met an index out of
+                               range, skipped the access and set the device error word */
 
 /* cfg.flags */
 #define SNN_STDP_OFF 1u      /* no depression / potentiation (sd stays 0) */

@@ -18,6 +18,11 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(PKG, "_build")
 LIB_PATH = os.path.join(BUILD_DIR, "libsnn.so")
+# the checked build (-DSNN_CHECKED): every step kernel verifies its computed
+# indices before use; a bad one sets the device error word (SNN_EBOUNDS) and
+# the access is skipped
+CHECKED_DIR = os.path.join(BUILD_DIR, "checked")
+CHECKED_LIB_PATH = os.path.join(BUILD_DIR, "libsnn_checked.so")
 SOURCES = ["snn_build.cu", "snn_step.cu", "snn_dense.cu", "snn_api.cu"]
 HEADERS = ["snn_internal.cuh"]
 
@@ -40,14 +45,18 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    os.makedirs(BUILD_DIR, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra_flags=(), checked: bool = False) -> str:
+    obj_dir = CHECKED_DIR if checked else BUILD_DIR
+    lib_path = CHECKED_LIB_PATH if checked else LIB_PATH
+    if checked:
+        extra_flags = tuple(extra_flags) + ("-DSNN_CHECKED",)
+    os.makedirs(obj_dir, exist_ok=True)
     headers = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(INCLUDE, "snn.h")]
     jobs = []
     objs = []
     for src in SOURCES:
         s = os.path.join(CSRC, src)
-        o = os.path.join(BUILD_DIR, src.replace(".cu", ".o"))
+        o = os.path.join(obj_dir, src.replace(".cu", ".o"))
         objs.append(o)
         if force or _stale(o, [s] + headers):
             jobs.append([nvcc(), *NVCC_FLAGS, *extra_flags, "-c", s, "-o", o])
@@ -64,13 +73,21 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
         for out in ex.map(run, jobs):
             if verbose and out.strip():
                 print(out)
-    if force or jobs or _stale(LIB_PATH, objs):
-        tmp = LIB_PATH + ".tmp%d" % os.getpid()
+    if force or jobs or _stale(lib_path, objs):
+        tmp = lib_path + ".tmp%d" % os.getpid()
         run([nvcc(), "-shared", *ARCH, "-Xcompiler", "-fPIC", "-o", tmp, *objs])
-        os.replace(tmp, LIB_PATH)
-    return LIB_PATH
+        os.replace(tmp, lib_path)
+    return lib_path
+
+
+def build_all(force: bool = False, verbose: bool = False):
+    """The library and its checked build, compiled side by side."""
+    with concurrent.futures.ThreadPoolExecutor(max_workers=2) as ex:
+        a = ex.submit(build, force, verbose)
+        b = ex.submit(build, force, verbose, (), True)
+        return a.result(), b.result()
 
 
 if __name__ == "__main__":
     import sys
-    print(build(force="--force" in sys.argv, verbose=True))
+    print(build_all(force="--force" in sys.argv, verbose=True))

@@ -724,7 +724,7 @@ int finish_run(snn_net *net)
     SNN_TRY(read_counters_raw(net, &hc));
     if (hc.error) {
         set_error("device error word %d", hc.error);
-        return hc.error == SNN_ETIMEOUT ? SNN_ETIMEOUT : SNN_ECUDA;
+        return (hc.error == SNN_ETIMEOUT || hc.error == SNN_EBOUNDS) ? hc.error : SNN_ECUDA;
     }
     return SNN_OK;
 }
@@ -913,6 +913,7 @@ const char *snn_strerror(int code)
     case SNN_ECUDA: return "CUDA error";
     case SNN_EOVERFLOW: return "Q16 current bound cannot be guaranteed";
     case SNN_ETIMEOUT: return "bounded device wait gave up";
+    case SNN_EBOUNDS: return "a kernel met an index out of range (checked build)";
     case SNN_ETRUNC: return "output truncated";
     case SNN_ESTATE: return "call does not fit the state of the handle";
     default: return "unknown error";
@@ -1306,7 +1307,7 @@ int snn_batch_run(snn_batch *b, uint32_t n_ms)
         SNN_TRY(read_counters_raw(n, &hc));
         if (hc.error && rc == SNN_OK) {
             set_error("device error word %d", hc.error);
-            rc = hc.error == SNN_ETIMEOUT ? SNN_ETIMEOUT : SNN_ECUDA;
+            rc = (hc.error == SNN_ETIMEOUT || hc.error == SNN_EBOUNDS) ? hc.error : SNN_ECUDA;
         }
     }
     return rc;

@@ -48,8 +48,10 @@ __device__ __forceinline__ void dense_row_walk(const DevNet &n, int64_t base, in
     // search so that the search runs under their latency
     const bool row_w = kDeriv || fbits != 0;
     const bool row_sd = kExc && (kDeriv || ltp_on || (stdp && fbits != 0));
+    const uint32_t staged = kSlots * n.npc;
     for (int c = lane; c * 8 < m; c += 32) {
         const int k0 = c * 8;
+        if (out_of_range(n, base + k0 + 8 <= n.S)) continue;
         const uint4 tv = rt4[c];
         int4 wa = make_int4(0, 0, 0, 0), wb = wa, sa = wa, sb = wa;
         if (row_w) {
@@ -100,6 +102,7 @@ __device__ __forceinline__ void dense_row_walk(const DevNet &n, int64_t base, in
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
                 const uint32_t v = (u & 1) ? (tw[u >> 1] >> 16) : (tw[u >> 1] & 0xffffu);
+                if (out_of_range(n, v < staged)) continue;
                 if ((fmask >> u) & 1u) atomicAdd(&s_in[v], wv[u]);
             }
             continue;
@@ -110,6 +113,7 @@ __device__ __forceinline__ void dense_row_walk(const DevNet &n, int64_t base, in
         for (int u = 0; u < 8; ++u) {
             const bool f = (fmask >> u) & 1u;
             const uint32_t v = (u & 1) ? (tw[u >> 1] >> 16) : (tw[u >> 1] & 0xffffu);
+            if (out_of_range(n, v < staged)) continue;
             const uint32_t x = s_x[v];
             int32_t sdv = sv[u];
             if ((x & kFiredLast) && am[u]) {
@@ -239,15 +243,17 @@ __global__ void __launch_bounds__(1024) k_dense(DevNet n, const int *t_now)
                 // inhibitory row of a generated net: one bucket (delay 1), one
                 // weight, nothing plastic
                 if (fbits & 2u) {
-                    const uint4 *rt4 = reinterpret_cast<const uint4 *>(n.tgt16 + row_base(n, p));
+                    const int64_t base = row_base(n, p);
+                    const uint4 *rt4 = reinterpret_cast<const uint4 *>(n.tgt16 + base);
                     for (int c = lane; c * 8 < m; c += 32) {
+                        if (out_of_range(n, base + c * 8 + 8 <= n.S)) continue;
                         const uint4 tv = rt4[c];
                         const int nv = min(8, m - c * 8);
                         const uint32_t tw[4] = {tv.x, tv.y, tv.z, tv.w};
     #pragma unroll
                         for (int u = 0; u < 8; ++u) {
                             const uint32_t v = (u & 1) ? (tw[u >> 1] >> 16) : (tw[u >> 1] & 0xffffu);
-                            if (u < nv) atomicAdd(&s_in[v], n.w_inh);
+                            if (u < nv && !out_of_range(n, v < kSlots * npc)) atomicAdd(&s_in[v], n.w_inh);
                         }
                     }
                 }

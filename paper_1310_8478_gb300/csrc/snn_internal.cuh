@@ -231,6 +231,22 @@ __device__ __forceinline__ bool dense_selected(const DevNet &n, int t)
     return (uint32_t)(n.ring_cnt[2 * slot] + n.ring_cnt[2 * slot + 1]) >= n.dense_min_spikes;
 }
 
+// Checked builds (-DSNN_CHECKED) verify every computed index before use: a
+// bad one sets the device error word to SNN_EBOUNDS (first error kept) and the
+// caller skips the access.  Other builds compile the checks out.
+#ifdef SNN_CHECKED
+__device__ __forceinline__ bool out_of_range(const DevNet &n, bool ok)
+{
+    if (!ok) atomicCAS(&n.ctr->error, 0, SNN_EBOUNDS);
+    return !ok;
+}
+#else
+__device__ __forceinline__ bool out_of_range(const DevNet &, bool)
+{
+    return false;
+}
+#endif
+
 // a step without the dense pass delivers column by column through shared
 // memory when its expected events reach staged_min_events: excitatory spikes
 // of t - d reach bucket d (about M / D synapses), inhibitory spikes of t - 1

@@ -99,10 +99,12 @@ __global__ void __launch_bounds__(1024) k_deliver(DevNet n, const int *t_now)
             const bool inh = l >= (int)n.D;
             const int d = inh ? l - (int)n.D + 1 : l + 1;
             const uint32_t p = (uint32_t)(inh ? s_list[l][n.N - 1 - idx] : s_list[l][idx]);
-            const uint16_t *off = n.doff + (size_t)p * kDoffStride;
-            lo = row_base(n, p) + off[d - 1];
-            len = (int)off[d] - (int)off[d - 1];
-            info = (inh ? 0u : 1u) | ((p / n.npc) << 1);
+            if (!out_of_range(n, p < n.N)) {
+                const uint16_t *off = n.doff + (size_t)p * kDoffStride;
+                lo = row_base(n, p) + off[d - 1];
+                len = (int)off[d] - (int)off[d - 1];
+                info = (inh ? 0u : 1u) | ((p / n.npc) << 1);
+            }
         }
         int incl = len;
 #pragma unroll
@@ -135,10 +137,15 @@ __global__ void __launch_bounds__(1024) k_deliver(DevNet n, const int *t_now)
                 if (e < tile_len) {
                     while (w_start[j + 1] <= e) ++j;
                     k[u] = w_lo[j] + (e - w_start[j]);
+                    if (out_of_range(n, k[u] < n.S)) {
+                        k[u] = -1;
+                        continue;
+                    }
                     inf[u] = w_info[j];
                     wk[u] = n.w[k[u]];
                     sk[u] = ((inf[u] & 1u) && stdp) ? n.sd[k[u]] : 0;
                     tg[u] = target_gid(n, inf[u] >> 1, k[u]);
+                    if (out_of_range(n, tg[u] < n.N)) k[u] = -1;
                 }
             }
 #pragma unroll
@@ -277,8 +284,16 @@ __device__ __forceinline__ void deliver_cols(const DevNet &n, int t, int32_t *s_
                         if (e < tile_len) {
                             while (w_start[j + 1] <= e) ++j;
                             k[u] = cbase + w_lo[j] + (e - w_start[j]);
+                            if (out_of_range(n, k[u] < n.S)) {
+                                k[u] = -1;
+                                continue;
+                            }
                             ex[u] = w_exc[j] != 0;
                             v[u] = n.tgt16[k[u]];
+                            if (out_of_range(n, v[u] < kSlots * npc)) {
+                                k[u] = -1;
+                                continue;
+                            }
                             wk[u] = ex[u] ? n.w[k[u]] : n.w_inh;
                             sk[u] = (ex[u] && stdp) ? n.sd[k[u]] : 0;
                         }
@@ -392,7 +407,10 @@ __global__ void __launch_bounds__(1024) k_ltp(DevNet n, const int *t_now, int fo
         for (int64_t e0 = lo + lane; e0 < hi; e0 += 32 * kUnroll) {
             uint64_t r[kUnroll];
 #pragma unroll
-            for (int u = 0; u < kUnroll; ++u) r[u] = (e0 + 32 * u < hi) ? n.rin[e0 + 32 * u] : ~0ull;
+            for (int u = 0; u < kUnroll; ++u) {
+                r[u] = (e0 + 32 * u < hi && !out_of_range(n, e0 + 32 * u < n.n_rin)) ? n.rin[e0 + 32 * u] : ~0ull;
+                if (r[u] != ~0ull && out_of_range(n, (uint32_t)r[u] < n.N)) r[u] = ~0ull;
+            }
             uint2 h[kUnroll];
             int32_t sv[kUnroll];
 #pragma unroll
@@ -448,7 +466,9 @@ __global__ void __launch_bounds__(1024) k_fold(DevNet n, const int *t_now, int f
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 if (!v[u]) continue;
-                n.sd[row_base(n, (uint32_t)r[u]) + ((uint32_t)(r[u] >> 32) & 0xffffu)] += v[u];
+                const int64_t fwd = row_base(n, (uint32_t)r[u]) + ((uint32_t)(r[u] >> 32) & 0xffffu);
+                if (out_of_range(n, (uint32_t)r[u] < n.N && fwd < n.S)) continue;
+                n.sd[fwd] += v[u];
                 n.sd_rev[e0 + u * (int64_t)blockDim.x] = 0;
             }
         }
@@ -649,8 +669,8 @@ __device__ __forceinline__ void neuron_body(const DevNet &n, const int *t_now, i
             const uint32_t i = first + it * blockDim.x + threadIdx.x;
             const bool e = (fe >> it) & 1u, q = (fi >> it) & 1u;
             if (!(e || q)) continue;
-            if (e) ring[pe++] = (int32_t)i;
-            else ring[n.N - 1 - (pi++)] = (int32_t)i;
+            const int pos = e ? pe++ : (int)n.N - 1 - (pi++);
+            if (!out_of_range(n, pos >= 0 && pos < (int)n.N)) ring[pos] = (int32_t)i;
             const unsigned long long r = rbase + (unsigned long long)(pr++);
             if (r < n.raster_cap) n.raster_gid[r] = (int32_t)i;
         }

@@ -21,7 +21,7 @@ STDP_OFF = 1
 DELIVERY_OFF = 2
 FP64 = 4
 
-OK, EINVAL, ENOMEM, ECUDA, EOVERFLOW, ETIMEOUT, ETRUNC, ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
+OK, EINVAL, ENOMEM, ECUDA, EOVERFLOW, ETIMEOUT, ETRUNC, ESTATE, EBOUNDS = 0, -1, -2, -3, -4, -5, -6, -7, -8
 SNN_NOALLOC_MAX_SYNAPSES = 1 << 20   # staging size of snn_read_synapses_noalloc
 
 
@@ -130,20 +130,26 @@ _SIGS = {
 _lib = None
 
 
+def checked() -> bool:
+    """SNN_CHECKED=1 in the environment selects the checked build."""
+    return os.environ.get("SNN_CHECKED", "") == "1"
+
+
 def library_path() -> str:
-    return _build.LIB_PATH
+    return _build.CHECKED_LIB_PATH if checked() else _build.LIB_PATH
 
 
 def load(build_if_missing: bool = True):
-    """Load libsnn.so (building it first if needed); raises if impossible."""
+    """Load libsnn.so, or libsnn_checked.so under SNN_CHECKED=1 (building it
+    first if needed); raises if impossible."""
     global _lib
     if _lib is not None:
         return _lib
-    path = _build.LIB_PATH
+    path = library_path()
     if not os.path.exists(path):
         if not build_if_missing:
             raise RuntimeError("CUDA engine library missing: %s (run build())" % path)
-        _build.build()
+        _build.build(checked=checked())
     lib = ctypes.CDLL(path)
     for name, (res, args) in _SIGS.items():
         f = getattr(lib, name)
@@ -197,6 +203,40 @@ def _stream_handle(stream):
 # ---------------------------------------------------------------------------
 # C-ABI mirrors (same names as include/snn.h)
 # ---------------------------------------------------------------------------
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+_allocator_refs = None          # the installed callbacks, kept alive while in use
+
+
+def set_allocator(alloc=None, free=None):
+    """snn_set_allocator with Python callables: alloc(nbytes, stream_handle) ->
+    device pointer as int (0 on failure), free(ptr).  Nets built afterwards
+    allocate through them (blocks must be 256-byte aligned); None restores
+    cudaMalloc / cudaFree."""
+    global _allocator_refs
+    lib = load()
+    if alloc is None:
+        lib.snn_set_allocator(None, None, None)
+        _allocator_refs = None
+        return
+    a = _ALLOC_FN(lambda n, stream, ctx: alloc(int(n), stream or 0) or None)
+    f = _FREE_FN(lambda ptr, ctx: free(int(ptr)))
+    lib.snn_set_allocator(ctypes.cast(a, ctypes.c_void_p), ctypes.cast(f, ctypes.c_void_p), None)
+    _allocator_refs = (a, f)
+
+
+def torch_allocator():
+    """(alloc, free) on PyTorch's caching allocator, for set_allocator."""
+    import torch
+
+    def alloc(n, stream):
+        return torch.cuda.caching_allocator_alloc(n, torch.cuda.current_device(), stream)
+
+    def free(ptr):
+        torch.cuda.caching_allocator_delete(ptr)
+    return alloc, free
+
+
 def snn_build_network(cfg: dict, stream=None, hbm_budget_bytes: int = 0, raster_capacity=None):
     lib = load()
     h = ctypes.c_void_p()
