@@ -36,10 +36,29 @@ constexpr uint32_t kDepMask = 0x7fffu;
 // chunk spread over three or more buckets walks them position by position.
 // kDeriv: the step closes a plasticity period (the long-term update runs
 // between LTP and delivery) -- excitatory rows only.
+// Bulk prefetch of [p, p + bytes) into L2 (p 16-byte aligned, bytes a
+// multiple of 16); nothing waits on it.
+__device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// The 256 synapses from position k (a multiple of 8) into L2: targets, and
+// weights and derivatives when asked.
+__device__ __forceinline__ void prefetch_segment(const DevNet &n, int64_t k, bool w, bool sd)
+{
+    if (k >= n.S) return;
+    const uint32_t cnt = (uint32_t)min((int64_t)256, n.S - k);
+    prefetch_l2(n.tgt16 + k, cnt * 2u);
+    if (w) prefetch_l2(n.w + k, cnt * 4u);
+    if (sd) prefetch_l2(n.sd + k, cnt * 4u);
+}
+
 template <bool kExc, bool kDeriv>
 __device__ __forceinline__ void dense_row_walk(const DevNet &n, int64_t base, int m, int D, float scale, uint32_t fbits,
                                                bool stdp, bool ltp_on, const int32_t *w_off, const int32_t *w_amt,
-                                               int32_t *s_in, const uint16_t *s_x, int lane)
+                                               int32_t *s_in, const uint16_t *s_x, int lane, int64_t next_base,
+                                               bool next_exc)
 {
     const uint4 *rt4 = reinterpret_cast<const uint4 *>(n.tgt16 + base);
     int4 *rw4 = reinterpret_cast<int4 *>(n.w + base);
@@ -51,6 +70,12 @@ __device__ __forceinline__ void dense_row_walk(const DevNet &n, int64_t base, in
     const uint32_t staged = kSlots * n.npc;
     for (int c = lane; c * 8 < m; c += 32) {
         const int k0 = c * 8;
+        // the warp's next 256 synapses (or the start of its next row) go to
+        // L2 while this chunk is processed: a pipeline that costs no registers
+        if (lane == 0) {
+            if (k0 + 256 < m) prefetch_segment(n, base + k0 + 256, row_w, row_sd);
+            else if (next_base >= 0) prefetch_segment(n, next_base, true, next_exc);
+        }
         if (out_of_range(n, base + k0 + 8 <= n.S)) continue;
         const uint4 tv = rt4[c];
         int4 wa = make_int4(0, 0, 0, 0), wb = wa, sa = wa, sb = wa;
@@ -250,7 +275,7 @@ __global__ void __launch_bounds__(1024) k_dense(DevNet n, const int *t_now)
                         const uint4 tv = rt4[c];
                         const int nv = min(8, m - c * 8);
                         const uint32_t tw[4] = {tv.x, tv.y, tv.z, tv.w};
-    #pragma unroll
+#pragma unroll
                         for (int u = 0; u < 8; ++u) {
                             const uint32_t v = (u & 1) ? (tw[u >> 1] >> 16) : (tw[u >> 1] & 0xffffu);
                             if (u < nv && !out_of_range(n, v < kSlots * npc)) atomicAdd(&s_in[v], n.w_inh);
@@ -260,15 +285,17 @@ __global__ void __launch_bounds__(1024) k_dense(DevNet n, const int *t_now)
             } else if (busy) {
                 const float scale = (float)D / (float)m;
                 const int64_t base = row_base(n, p);     // a multiple of 8: rows are padded
+                const int64_t nbase = r + nwarps < r1 ? row_base(n, p + nwarps) : -1;
+                const bool nexc = r + nwarps < n.ne;
                 if (!exc)
                     dense_row_walk<false, false>(n, base, m, D, scale, fbits, stdp, ltp_on, w_off, w_amt, s_in, s_x,
-                                                 lane);
+                                                 lane, nbase, nexc);
                 else if (deriv_on)
                     dense_row_walk<true, true>(n, base, m, D, scale, fbits, stdp, ltp_on, w_off, w_amt, s_in, s_x,
-                                               lane);
+                                               lane, nbase, nexc);
                 else
                     dense_row_walk<true, false>(n, base, m, D, scale, fbits, stdp, ltp_on, w_off, w_amt, s_in, s_x,
-                                                lane);
+                                                lane, nbase, nexc);
             }
             __syncwarp();
         }
