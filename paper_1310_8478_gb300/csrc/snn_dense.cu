@@ -43,6 +43,8 @@ __device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes)
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
+constexpr int kPrefetchAhead = 1;   // segments of 256 synapses between a warp's loads and its prefetches
+
 // The 256 synapses from position k (a multiple of 8) into L2: targets, and
 // weights and derivatives when asked.
 __device__ __forceinline__ void prefetch_segment(const DevNet &n, int64_t k, bool w, bool sd)
@@ -70,11 +72,13 @@ __device__ __forceinline__ void dense_row_walk(const DevNet &n, int64_t base, in
     const uint32_t staged = kSlots * n.npc;
     for (int c = lane; c * 8 < m; c += 32) {
         const int k0 = c * 8;
-        // the warp's next 256 synapses (or the start of its next row) go to
-        // L2 while this chunk is processed: a pipeline that costs no registers
+        // the warp's next 256-synapse segment (in this row or at the
+        // start of its next row) goes to L2 while this chunk is processed: a
+        // pipeline that costs no registers
         if (lane == 0) {
-            if (k0 + 256 < m) prefetch_segment(n, base + k0 + 256, row_w, row_sd);
-            else if (next_base >= 0) prefetch_segment(n, next_base, true, next_exc);
+            const int ka = k0 + kPrefetchAhead * 256, mr = (m + 255) & ~255;
+            if (ka < m) prefetch_segment(n, base + ka, row_w, row_sd);
+            else if (next_base >= 0) prefetch_segment(n, next_base + (ka - mr), true, next_exc);
         }
         if (out_of_range(n, base + k0 + 8 <= n.S)) continue;
         const uint4 tv = rt4[c];
@@ -208,6 +212,12 @@ __global__ void __launch_bounds__(1024) k_dense(DevNet n, const int *t_now)
         const uint32_t r0 = (unit - col * chunks) * n.dense_rows;
         const uint32_t r1 = min(npc, r0 + n.dense_rows);
         if (threadIdx.x < kSlots) s_col[threadIdx.x] = (uint32_t)n.nbr[col * kSlotStride + threadIdx.x];
+        // every warp's first row starts streaming into L2 while the block stages
+        if (lane == 0 && r0 + warp < r1) {
+            const int64_t b = row_base(n, col * npc + r0 + warp);
+            for (int sgm = 0; sgm < kPrefetchAhead; ++sgm)
+                prefetch_segment(n, b + sgm * 256, true, r0 + warp < n.ne);
+        }
         __syncthreads();
         for (int sl = 0; sl < kSlots; ++sl) {
             const int32_t *ls = n.last_spike + (size_t)s_col[sl] * npc;
@@ -270,7 +280,13 @@ __global__ void __launch_bounds__(1024) k_dense(DevNet n, const int *t_now)
                 if (fbits & 2u) {
                     const int64_t base = row_base(n, p);
                     const uint4 *rt4 = reinterpret_cast<const uint4 *>(n.tgt16 + base);
+                    const int64_t nbase = r + nwarps < r1 ? row_base(n, p + nwarps) : -1;
                     for (int c = lane; c * 8 < m; c += 32) {
+                        if (lane == 0) {        // next segment of targets, as in the row walk
+                            const int ka = c * 8 + 256, mr = (m + 255) & ~255;
+                            if (ka < m) prefetch_segment(n, base + ka, false, false);
+                            else if (nbase >= 0) prefetch_segment(n, nbase + (ka - mr), false, false);
+                        }
                         if (out_of_range(n, base + c * 8 + 8 <= n.S)) continue;
                         const uint4 tv = rt4[c];
                         const int nv = min(8, m - c * 8);
