@@ -36,13 +36,6 @@ constexpr uint32_t kDepMask = 0x7fffu;
 // chunk spread over three or more buckets walks them position by position.
 // kDeriv: the step closes a plasticity period (the long-term update runs
 // between LTP and delivery) -- excitatory rows only.
-// Bulk prefetch of [p, p + bytes) into L2 (p 16-byte aligned, bytes a
-// multiple of 16); nothing waits on it.
-__device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes)
-{
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
-}
-
 constexpr int kPrefetchAhead = 1;   // segments of 256 synapses between a warp's loads and its prefetches
 
 // The 256 synapses from position k (a multiple of 8) into L2: targets, and

@@ -328,6 +328,20 @@ __device__ __forceinline__ int32_t deriv_sd(const DevNet &n, int32_t s)
     return (int32_t)(((long long)s * n.deriv_decay + 32768) >> 16);
 }
 
+// Bulk prefetch of [p, p + bytes) into L2 (p 16-byte aligned, bytes a
+// multiple of 16); nothing waits on it.
+__device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// The 16-byte-aligned part of [p, p + bytes) into L2 (never past either end).
+__device__ __forceinline__ void prefetch_inside(const void *p, size_t bytes)
+{
+    const uintptr_t a = ((uintptr_t)p + 15u) & ~(uintptr_t)15u, b = ((uintptr_t)p + bytes) & ~(uintptr_t)15u;
+    if (b > a) prefetch_l2(reinterpret_cast<const void *>(a), (uint32_t)(b - a));
+}
+
 // thalamic drive (thal_per_col events per column, Philox keyed by (t, col))
 // and the external events of step t, by the threads of a whole grid
 __device__ __forceinline__ void drive(const DevNet &n, int t, uint32_t gtid, uint32_t gthreads)

@@ -398,10 +398,36 @@ __global__ void __launch_bounds__(1024) k_ltp(DevNet n, const int *t_now, int fo
     const int32_t *ring = n.ring_ids + (size_t)slot * n.N;
     const int lane = threadIdx.x & 31;
     const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
-    for (uint32_t item = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; item < (uint32_t)total;
-         item += warps) {
-        const int32_t post = (int)item < ce ? ring[item] : ring[n.N - 1 - ((int)item - ce)];
-        const int64_t lo = n.rin_off[post], hi = n.rin_off[post + 1];
+    auto spiker = [&](uint32_t item) -> int32_t {
+        return (int)item < ce ? ring[item] : ring[n.N - 1 - ((int)item - ce)];
+    };
+    // the reverse-entry ranges of the warp's next two spikers are known one
+    // item ahead, and the next one's entries go to L2 while this one is walked
+    const uint32_t first = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t lo1 = 0, hi1 = 0, lo2 = 0, hi2 = 0;
+    if (first < (uint32_t)total) {
+        const int32_t p = spiker(first);
+        lo1 = n.rin_off[p];
+        hi1 = n.rin_off[p + 1];
+    }
+    if (first + warps < (uint32_t)total) {
+        const int32_t p = spiker(first + warps);
+        lo2 = n.rin_off[p];
+        hi2 = n.rin_off[p + 1];
+    }
+    for (uint32_t item = first; item < (uint32_t)total; item += warps) {
+        const int64_t lo = lo1, hi = hi1;
+        lo1 = lo2;
+        hi1 = hi2;
+        if (lane == 0 && hi1 > lo1) {
+            prefetch_inside(n.rin + lo1, (size_t)(hi1 - lo1) * 8);
+            prefetch_inside(n.sd_rev + lo1, (size_t)(hi1 - lo1) * 4);
+        }
+        if (item + 2 * warps < (uint32_t)total) {
+            const int32_t p = spiker(item + 2 * warps);
+            lo2 = n.rin_off[p];
+            hi2 = n.rin_off[p + 1];
+        }
         // kUnroll entries per lane: reverse entries, then the sources'
         // histories and the synapses' derivatives (independent) in one round
         for (int64_t e0 = lo + lane; e0 < hi; e0 += 32 * kUnroll) {
