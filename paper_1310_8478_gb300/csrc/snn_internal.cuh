@@ -21,7 +21,7 @@ constexpr uint32_t kMaxCompactNpc = 4096;    // compact targets slot * npc + loc
 constexpr uint32_t kMinCompactNpc = 2;       // the slot reciprocal ceil(2^32 / npc) fits 32 bits
 constexpr uint32_t kDenseMaxNpc = 2800;      // staged columns must fit in shared memory
 static_assert(kSlots * kMaxCompactNpc <= 65536, "compact targets must fit 16 bits");
-constexpr int kUnroll = 4;                   // dense pass: positions per lane in flight
+constexpr int kUnroll = 4;                   // event-driven walks: synapses per lane in flight
 
 // Device counters and per-step bookkeeping (one struct, device memory).
 struct DevCounters {

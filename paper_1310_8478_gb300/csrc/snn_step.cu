@@ -24,10 +24,11 @@
 //       per-synapse order LTP(t-1) -> long-term update -> delivery + LTD(t),
 //       with the target columns' input and post-spike state staged in shared
 //       memory.
-// The choice is taken on the device from the number of spikes of step t-1
-// (every kernel of the step reads the same count); both give bit-identical
-// results because all synaptic arithmetic is int32 and the per-synapse order
-// of the updates is the same.  An LTP still owed when a run ends is applied
+// The choice is taken on the device from the ring counts (the spikes of step
+// t-1 for the dense pass, the expected events of step t for the staged
+// delivery; every kernel of the step reads the same counts); all give
+// bit-identical results because all synaptic arithmetic is int32 and the
+// per-synapse order of the updates is the same.  An LTP still owed when a run ends is applied
 // by the host-side flush (k_ltp + k_deriv with force = 1) before any read.
 #include "snn_internal.cuh"
 
