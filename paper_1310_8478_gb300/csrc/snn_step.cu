@@ -192,7 +192,8 @@ __global__ void __launch_bounds__(1024) k_deliver(DevNet n, const int *t_now)
 //   stays in L2 (the ring-list order of k_deliver sweeps the whole torus once
 //   per delay instead).
 // ---------------------------------------------------------------------------
-constexpr int kTileWords = 32 + 33 + 32;     // per warp: item starts, length prefix, kinds
+constexpr int kItemCap = 96;                // per warp: pending (row, bucket) items
+constexpr int kTileWords = 32 + 33 + 32 + kItemCap;   // per warp: item starts, length prefix, kinds, pending items
 
 size_t staged_smem_bytes(uint32_t npc, uint32_t block)
 {
@@ -218,6 +219,7 @@ __device__ __forceinline__ void deliver_cols(const DevNet &n, int t, int32_t *s_
     int32_t *w_lo = s_tile + warp * kTileWords;                // [32] column-relative first synapse
     int32_t *w_start = w_lo + 32;                              // [33] prefix of the lengths
     int32_t *w_exc = w_start + 33;                             // [32] 1: excitatory row
+    uint32_t *w_items = reinterpret_cast<uint32_t *>(w_exc + 32);   // [kItemCap] pending items
     unsigned long long ev_all = 0, ev_exc = 0;
     for (uint32_t col = blockIdx.x; col < n.C;) {
         if (threadIdx.x < kSlots) s_col[threadIdx.x] = (uint32_t)n.nbr[col * kSlotStride + threadIdx.x];
@@ -237,100 +239,148 @@ __device__ __forceinline__ void deliver_cols(const DevNet &n, int t, int32_t *s_
             __syncthreads();
         }
         const int64_t cbase = (int64_t)col * npc * n.uniform_m;   // first synapse of the column
-        for (uint32_t rb = warp * 32; rb < npc; rb += nwarps * 32) {
-            const uint32_t r = rb + lane;
-            uint32_t fb = 0;                                       // bit d: the row's source fired at t - d
-            if (r < npc && deliver_on) fb = (n.hl[col * npc + r].x << 1) & (r < n.ne ? dmask_e : dmask_i);
-            while (__any_sync(0xffffffffu, fb != 0)) {
-                // every lane takes the lowest flagged bucket of its row
-                const int d = fb ? __ffs(fb) - 1 : 0;
-                fb &= fb - 1u;
-                int len = 0, lo = 0, exc = 0;
-                if (d) {
-                    const uint16_t *off = n.doff + (size_t)(col * npc + r) * kDoffStride;
-                    const int a = off[d - 1];
-                    len = (int)off[d] - a;
-                    lo = (int)(r * n.uniform_m) + a;
-                    exc = r < n.ne ? 1 : 0;
+        // one tile: lane i takes item (row r, bucket d) when valid, the warp
+        // prefix-sums the bucket lengths and walks the concatenated synapses
+        auto tile = [&](uint32_t r, int d, bool valid) {
+            int len = 0, lo = 0, exc = 0;
+            if (valid) {
+                const uint16_t *off = n.doff + (size_t)(col * npc + r) * kDoffStride;
+                const int a = off[d - 1];
+                len = (int)off[d] - a;
+                lo = (int)(r * n.uniform_m) + a;
+                exc = r < n.ne ? 1 : 0;
+            }
+            int incl = len;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const int tile_len = __shfl_sync(0xffffffffu, incl, 31);
+            const int exc_len = __reduce_add_sync(0xffffffffu, exc ? len : 0);
+            w_lo[lane] = lo;
+            w_start[lane] = incl - len;
+            w_exc[lane] = exc;
+            if (lane == 0) {
+                w_start[32] = tile_len;
+                ev_all += (unsigned long long)tile_len;
+                ev_exc += (unsigned long long)exc_len;
+            }
+            __syncwarp();
+            // kUnroll synapses per lane in flight: targets, weights and
+            // derivatives first, then the updates
+            int j = 0;
+            for (int e0 = lane; e0 < tile_len; e0 += 32 * kUnroll) {
+                int64_t k[kUnroll];
+                uint32_t v[kUnroll];
+                int32_t wk[kUnroll], sk[kUnroll], ls[kUnroll];
+                bool ex[kUnroll];
+#pragma unroll
+                for (int u = 0; u < kUnroll; ++u) {
+                    const int e = e0 + 32 * u;
+                    k[u] = -1;
+                    if (e < tile_len) {
+                        while (w_start[j + 1] <= e) ++j;
+                        k[u] = cbase + w_lo[j] + (e - w_start[j]);
+                        if (out_of_range(n, k[u] < n.S)) {
+                            k[u] = -1;
+                            continue;
+                        }
+                        ex[u] = w_exc[j] != 0;
+                        v[u] = n.tgt16[k[u]];
+                        if (out_of_range(n, v[u] < kSlots * npc)) {
+                            k[u] = -1;
+                            continue;
+                        }
+                        wk[u] = ex[u] ? n.w[k[u]] : n.w_inh;
+                        sk[u] = (ex[u] && stdp) ? n.sd[k[u]] : 0;
+                    }
                 }
-                int incl = len;
+                if (kStage) {
+#pragma unroll
+                    for (int u = 0; u < kUnroll; ++u) {
+                        if (k[u] < 0) continue;
+                        atomicAdd(&s_in[v[u]], wk[u]);
+                        if (ex[u] && stdp) {
+                            const int32_t a = s_x[v[u]];
+                            if (a) n.sd[k[u]] = sk[u] - a;
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int u = 0; u < kUnroll; ++u) {
+                        if (k[u] < 0) continue;
+                        const uint32_t slot = __umulhi(v[u], n.npc_recip);
+                        v[u] = s_col[slot] * npc + (v[u] - slot * npc);      // target gid
+                        red_add(&n.I[v[u]], wk[u]);
+                        ls[u] = (ex[u] && stdp) ? n.last_spike[v[u]] : 0;
+                    }
+#pragma unroll
+                    for (int u = 0; u < kUnroll; ++u) {
+                        if (k[u] < 0 || !(ex[u] && stdp)) continue;
+                        const int lag = t - ls[u];                         // >= 1
+                        if (lag < kLut) {
+                            const int32_t a = s_lut[lag];
+                            if (a) n.sd[k[u]] = sk[u] - a;
+                        }
+                    }
+                }
+            }
+            __syncwarp();
+        };
+        // Items (row << 5 | bucket) collect in the warp's buffer across row
+        // groups and are walked 32 at a time, so that a tile is full even when
+        // few rows of a group fired; a group with too many items for the
+        // buffer is walked directly, one flagged bucket per lane and pass.
+        int cnt = 0;                                   // items in the buffer
+        uint32_t rb = warp * 32;                       // next row group to scan
+        uint32_t fb = 0, r = 0;                        // a group walked directly: its remaining flags
+        for (;;) {
+            uint32_t tr = 0;
+            int td = 0;
+            bool tv = false;
+            if (__any_sync(0xffffffffu, fb != 0)) {
+                // direct walk: every lane takes the lowest flagged bucket of its row
+                td = fb ? __ffs(fb) - 1 : 0;
+                fb &= fb - 1u;
+                tr = r;
+                tv = td != 0;
+            } else if (cnt >= 32 || (cnt > 0 && rb >= npc)) {
+                const int take = min(cnt, 32);
+                cnt -= take;
+                const uint32_t it = lane < take ? w_items[cnt + lane] : 0u;
+                tr = it >> 5;
+                td = (int)(it & 31u);
+                tv = lane < take;
+            } else if (rb < npc) {
+                r = rb + lane;
+                rb += nwarps * 32;
+                uint32_t f = 0;                        // bit d: the row's source fired at t - d
+                if (r < npc && deliver_on) f = (n.hl[col * npc + r].x << 1) & (r < n.ne ? dmask_e : dmask_i);
+                const int mine = __popc(f);
+                int incl = mine;
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1) {
                     const int y = __shfl_up_sync(0xffffffffu, incl, o);
                     if (lane >= o) incl += y;
                 }
-                const int tile_len = __shfl_sync(0xffffffffu, incl, 31);
-                const int exc_len = __reduce_add_sync(0xffffffffu, exc ? len : 0);
-                w_lo[lane] = lo;
-                w_start[lane] = incl - len;
-                w_exc[lane] = exc;
-                if (lane == 0) {
-                    w_start[32] = tile_len;
-                    ev_all += (unsigned long long)tile_len;
-                    ev_exc += (unsigned long long)exc_len;
-                }
-                __syncwarp();
-                // kUnroll synapses per lane in flight: targets, weights and
-                // derivatives first, then the updates
-                int j = 0;
-                for (int e0 = lane; e0 < tile_len; e0 += 32 * kUnroll) {
-                    int64_t k[kUnroll];
-                    uint32_t v[kUnroll];
-                    int32_t wk[kUnroll], sk[kUnroll], ls[kUnroll];
-                    bool ex[kUnroll];
-#pragma unroll
-                    for (int u = 0; u < kUnroll; ++u) {
-                        const int e = e0 + 32 * u;
-                        k[u] = -1;
-                        if (e < tile_len) {
-                            while (w_start[j + 1] <= e) ++j;
-                            k[u] = cbase + w_lo[j] + (e - w_start[j]);
-                            if (out_of_range(n, k[u] < n.S)) {
-                                k[u] = -1;
-                                continue;
-                            }
-                            ex[u] = w_exc[j] != 0;
-                            v[u] = n.tgt16[k[u]];
-                            if (out_of_range(n, v[u] < kSlots * npc)) {
-                                k[u] = -1;
-                                continue;
-                            }
-                            wk[u] = ex[u] ? n.w[k[u]] : n.w_inh;
-                            sk[u] = (ex[u] && stdp) ? n.sd[k[u]] : 0;
-                        }
+                const int total = __shfl_sync(0xffffffffu, incl, 31);
+                if (cnt + total <= kItemCap) {
+                    int pos = cnt + incl - mine;
+                    while (f) {
+                        w_items[pos++] = (r << 5) | (uint32_t)(__ffs(f) - 1);
+                        f &= f - 1u;
                     }
-                    if (kStage) {
-#pragma unroll
-                        for (int u = 0; u < kUnroll; ++u) {
-                            if (k[u] < 0) continue;
-                            atomicAdd(&s_in[v[u]], wk[u]);
-                            if (ex[u] && stdp) {
-                                const int32_t a = s_x[v[u]];
-                                if (a) n.sd[k[u]] = sk[u] - a;
-                            }
-                        }
-                    } else {
-#pragma unroll
-                        for (int u = 0; u < kUnroll; ++u) {
-                            if (k[u] < 0) continue;
-                            const uint32_t slot = __umulhi(v[u], n.npc_recip);
-                            v[u] = s_col[slot] * npc + (v[u] - slot * npc);      // target gid
-                            red_add(&n.I[v[u]], wk[u]);
-                            ls[u] = (ex[u] && stdp) ? n.last_spike[v[u]] : 0;
-                        }
-#pragma unroll
-                        for (int u = 0; u < kUnroll; ++u) {
-                            if (k[u] < 0 || !(ex[u] && stdp)) continue;
-                            const int lag = t - ls[u];                         // >= 1
-                            if (lag < kLut) {
-                                const int32_t a = s_lut[lag];
-                                if (a) n.sd[k[u]] = sk[u] - a;
-                            }
-                        }
-                    }
+                    cnt += total;
+                    __syncwarp();
+                } else {
+                    fb = f;                            // too many for the buffer: walk this group directly
                 }
-                __syncwarp();
+                continue;
+            } else {
+                break;
             }
+            tile(tr, td, tv);
         }
         __syncthreads();
         if (kStage) {
