@@ -124,7 +124,8 @@ typedef struct {
     uint32_t dense_block;            /* threads per block of the dense synapse pass (32..1024) */
     uint32_t dense_rows;             /* source rows per block of the dense pass */
     uint32_t dense_permille;         /* a step takes the dense pass when at least this many
-                                        neurons per 1000 fired in the step before; 1001 = never */
+                                        neurons per 1000 fired in the step before (default 250,
+                                        the measured crossover); 1001 = never */
     uint32_t staged_permille;        /* a step without the dense pass delivers column by column
                                         through shared memory when its expected events (spikes of
                                         the last max_delay steps x fan-out / max_delay, plus
