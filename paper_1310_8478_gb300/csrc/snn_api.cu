@@ -629,7 +629,6 @@ void launch_step(snn_net *net, int32_t t, cudaStream_t s)
     const snn_launch &L = net->launch;
     const bool prof = net->profile;
     const uint32_t P = net->cfg.deriv_period_ms;
-    (void)P;
     auto mark = [&](int kind) {
         if (prof) cudaEventRecord(next_event(net, kind), s);
     };
