@@ -332,6 +332,10 @@ def main():
     if rank == 0 and not args.no_cpu_baseline:
         cpu = oracle_sample(args.cpu_seconds)      # before any GPU work; same process, no fork
 
+    # rank 0 compiles whatever is stale; the other ranks then find it built
+    if rank == 0:
+        eng.build_engine()
+    barrier()
     eng.build_engine()
     cfg = workloads.workload(args.workload)
     K, W = args.steps, args.warmup
