@@ -15,7 +15,9 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 BUILD_DIR = os.path.join(HERE, "_build")
-LIB_PATH = os.path.join(BUILD_DIR, "liborc.so")
+# ORC_LIB names another build of oracle.c to load instead (the mutation test
+# of the pins loads deliberately broken copies this way)
+LIB_PATH = os.environ.get("ORC_LIB") or os.path.join(BUILD_DIR, "liborc.so")
 
 STDP_OFF = 1
 DELIVERY_OFF = 2
@@ -48,6 +50,8 @@ class OrcStim(ctypes.Structure):
 
 def build(force: bool = False) -> str:
     """Compile oracle.c into _build/liborc.so (gcc, no FMA contraction)."""
+    if os.environ.get("ORC_LIB"):
+        return LIB_PATH
     src = os.path.join(HERE, "oracle.c")
     hdr = os.path.join(HERE, "oracle.h")
     if (not force and os.path.exists(LIB_PATH)

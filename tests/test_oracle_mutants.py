@@ -1,0 +1,62 @@
+"""The pins of tests/test_oracle_pins.py and test_oracle_generator_pins.py
+are sensitive: each plausible
+mistake below, planted in a copy of the oracle on the CPU, makes at least
+one pin fail.  A mutant is oracle.c with one exact text replacement,
+compiled like the oracle and loaded in a child process through ORC_LIB."""
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+SRC = os.path.join(ROOT, "oracle", "oracle.c")
+
+MUTANTS = {
+    "ltd_sign": ("s->sd[syn] -= orc_stdp_q16(c->a_minus_mv", "s->sd[syn] += orc_stdp_q16(c->a_minus_mv"),
+    "ltp_lag_off_by_one": ("t - tp - d);", "t - tp - d + 1);"),
+    "ltp_window_excludes_arrival_now": ("latest_spike_at_or_before(s, pre, t - d, &tp)",
+                                        "latest_spike_at_or_before(s, pre, t - d - 1, &tp)"),
+    "deriv_bias_dropped": ("(int64_t)*w + (int64_t)bias_q16 + (int64_t)*sd", "(int64_t)*w + (int64_t)*sd"),
+    "deriv_decay_not_rounded": ("* (int64_t)decay_q16 + 32768)", "* (int64_t)decay_q16)"),
+    "one_v_substep": ("for (int half = 0; half < 2; ++half) {", "for (int half = 0; half < 1; ++half) {"),
+    "u_relaxes_to_c": ("    x = b * vv;                                  /* one 1 ms step of u */\n    x = x - uu;",
+                       "    x = b * vv;                                  /* one 1 ms step of u */\n    x = x - c;"),
+    "inhibitory_plastic_in_deriv": ("            if (!is_exc(s, p)) continue;\n            for (int64_t k = s->row_off[p]",
+                                    "            for (int64_t k = s->row_off[p]"),
+    "ring_member_index": ("(j - start) % 4u", "j % 4u"),
+    "thalamic_wrong_draw": ("return col * c->neurons_per_col + scale_draw(r[0], c->neurons_per_col);",
+                            "return col * c->neurons_per_col + scale_draw(r[1], c->neurons_per_col);"),
+    "inhibitory_delay_two": ("        *delay_out = 1;\n", "        *delay_out = 2;\n"),
+    "self_connection_allowed": ("if (tl >= local) tl += 1;", "(void)local;"),
+    "arrival_one_step_late": ("(t + s->dly[k]) % QUEUE_SLOTS", "(t + s->dly[k] + 1) % QUEUE_SLOTS"),
+    "delay_range_short": ("*delay_out = 1 + scale_draw(r[1], c->max_delay_ms);",
+                          "*delay_out = 1 + scale_draw(r[1], c->max_delay_ms - 1);"),
+    "current_scale": ("float cur = (float)current_q16 * 0x1p-16f;", "float cur = (float)current_q16 * 0x1p-15f;"),
+}
+
+
+@pytest.fixture(scope="module")
+def workdir(tmp_path_factory):
+    return tmp_path_factory.mktemp("mutants")
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_the_mutant(workdir, name):
+    old, new = MUTANTS[name]
+    text = open(SRC).read()
+    assert text.count(old) == 1, "mutation site not unique: %s" % name
+    d = workdir / name
+    d.mkdir()
+    shutil.copy(os.path.join(ROOT, "oracle", "oracle.h"), d / "oracle.h")
+    (d / "oracle.c").write_text(text.replace(old, new))
+    lib = d / "liborc.so"
+    subprocess.run(["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+                    "-o", str(lib), str(d / "oracle.c"), "-lm"], check=True)
+    env = dict(os.environ, ORC_LIB=str(lib))
+    pins = [os.path.join(HERE, f) for f in ("test_oracle_generator_pins.py", "test_oracle_pins.py")]
+    r = subprocess.run([sys.executable, "-m", "pytest", *pins, "-x", "-q", "-p", "no:cacheprovider"],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, "no pin failed for mutant %s:\n%s" % (name, r.stdout[-1500:])
