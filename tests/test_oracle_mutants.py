@@ -35,6 +35,15 @@ MUTANTS = {
     "delay_range_short": ("*delay_out = 1 + scale_draw(r[1], c->max_delay_ms);",
                           "*delay_out = 1 + scale_draw(r[1], c->max_delay_ms - 1);"),
     "current_scale": ("float cur = (float)current_q16 * 0x1p-16f;", "float cur = (float)current_q16 * 0x1p-15f;"),
+    "threshold_strict": ("if (vv >= 30.0f)", "if (vv > 30.0f)"),
+    "reset_double_d": ("if (vv >= 30.0f) { fired = 1; vv = c; uu = uu + d; }",
+                       "if (vv >= 30.0f) { fired = 1; vv = c; uu = uu + 2.0f * d; }"),
+    "current_halved_delivery": ("s->cur[post] += s->w[syn];", "s->cur[post] += s->w[syn] / 2;"),
+    "fs_a_like_rs": ("else            { *a = 0.1f;", "else            { *a = 0.02f;"),
+    "no_current_reset": ("s->cur[i] = 0;", ";"),
+    "wmax_clamp_missing": ("if (nw > wmax_q16) nw = wmax_q16;", ";"),
+    "negative_clamp_missing": ("if (nw < 0) nw = 0;", ";"),
+    "period_off_by_one": ("((uint32_t)t + 1) % c->deriv_period_ms == 0", "((uint32_t)t) % c->deriv_period_ms == 0"),
 }
 
 

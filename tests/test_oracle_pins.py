@@ -432,3 +432,85 @@ def test_fp64_physics_mode_rate_within_2_percent(orc):
     ra = len(a.raster()[0]) / 1250 / 2.0
     rb = len(b.raster()[0]) / 1250 / 2.0
     assert abs(ra - rb) <= 0.02 * ra, (ra, rb)
+
+
+# ---------------------------------------------------------------------------
+# delivery reaches the target's input in its arrival step; the threshold is
+# inclusive (Sec. 2: a synapse injects W at t_i + D; spike when v >= 30 mV)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("d,w_mv", [(1, 5), (3, 7), (20, 2)])
+def test_delivered_weight_enters_the_arrival_step(orc, d, w_mv):
+    # neuron 0 is forced to fire at t0; its one synapse (weight W, delay d)
+    # must add exactly W to neuron 1's input in step t0 + d and nothing in
+    # any other step: neuron 1's state then equals one neuron step with
+    # I = W from its previous state (the neuron step is pinned above), and
+    # the resting dynamics with I = 0 elsewhere
+    t0 = 30
+    w_q16 = w_mv * 65536
+    o = orc.Oracle(_pair_config(d), explicit=_pair_network(d, w_q16))
+    o.set_stimulus([t0], [0], [FORCE_Q16])
+    o.run(t0 + d)                                 # state after step t0 + d - 1
+    before = o.neurons()
+    v, u = np.float32(before["v"][1]), np.float32(before["u"][1])
+    o.run(1)                                      # step t0 + d
+    after = o.neurons()
+    v1, u1, fired = orc.neuron_step(v, u, w_q16, True)
+    assert not fired
+    assert after["v"][1].view(np.int32) == np.float32(v1).view(np.int32)
+    assert after["u"][1].view(np.int32) == np.float32(u1).view(np.int32)
+    # without the arrival the same step would have left the neuron elsewhere
+    v0, _, _ = orc.neuron_step(v, u, 0, True)
+    assert np.float32(v0) != np.float32(v1)
+
+
+def _two_substeps_f32(v, u, cur):
+    """Reading 2's v update in float32, one rounding per written operation."""
+    f = np.float32
+    for _ in range(2):
+        x = f(f(0.04) * v)
+        x = f(x + f(5.0))
+        x = f(x * v)
+        x = f(x + f(140.0))
+        x = f(x - u)
+        x = f(x + cur)
+        x = f(f(0.5) * x)
+        v = f(v + x)
+    return v
+
+
+def test_threshold_is_inclusive(orc):
+    # find states whose v lands exactly on 30 mV after the two substeps (the
+    # update itself is pinned above); the rule v >= 30 must fire there, and a
+    # state landing one float32 step below must not
+    rng = np.random.default_rng(77)
+    found = below = 0
+    for _ in range(400):
+        u = np.float32(rng.uniform(-14.0, -10.0))
+        cur_q16 = int(rng.integers(0, 20 * 65536))
+        cur = np.float32(cur_q16 * 2.0 ** -16)
+        # the starting v whose two substeps end on 30 mV, by bisection in
+        # float64 (the map increases for v above -62.5 mV), then every float32
+        # within 64 steps of it
+        lo, hi = -60.0, 30.0
+        for _ in range(80):
+            mid = 0.5 * (lo + hi)
+            x = mid
+            for _ in range(2):
+                x = x + 0.5 * (0.04 * x * x + 5.0 * x + 140.0 - float(u) + float(cur))
+            lo, hi = (mid, hi) if x < 30.0 else (lo, mid)
+        bits = np.array([lo], np.float32).view(np.int32)[0] + np.arange(-64, 65, dtype=np.int32)
+        v = bits.view(np.float32)
+        out = _two_substeps_f32(v, u, cur)
+        for vi in v[out == np.float32(30.0)][:1]:
+            v1, u1, fired = orc.neuron_step(np.float32(vi), u, cur_q16, True)
+            assert fired, (float(vi), cur_q16)
+            assert np.float32(v1) == np.float32(-65.0)
+            found += 1
+        for vi in v[out == np.nextafter(np.float32(30.0), np.float32(0.0))][:1]:
+            v1, u1, fired = orc.neuron_step(np.float32(vi), u, cur_q16, True)
+            assert not fired, (float(vi), cur_q16)
+            below += 1
+        if found >= 5 and below >= 5:
+            break
+    assert found >= 1, "no state reaching exactly 30 mV was found"
+    assert below >= 1, "no state reaching the float32 just below 30 mV was found"
