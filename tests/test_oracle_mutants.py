@@ -44,6 +44,35 @@ MUTANTS = {
     "wmax_clamp_missing": ("if (nw > wmax_q16) nw = wmax_q16;", ";"),
     "negative_clamp_missing": ("if (nw < 0) nw = 0;", ";"),
     "period_off_by_one": ("((uint32_t)t + 1) % c->deriv_period_ms == 0", "((uint32_t)t) % c->deriv_period_ms == 0"),
+    "ltd_uses_tau_plus": ('orc_stdp_q16(c->a_minus_mv, c->tau_minus_ms, t - tl)',
+                          'orc_stdp_q16(c->a_minus_mv, c->tau_plus_ms, t - tl)'),
+    "ltp_uses_a_minus": ('orc_stdp_q16(c->a_plus_mv, c->tau_plus_ms, t - tp - d)',
+                         'orc_stdp_q16(c->a_minus_mv, c->tau_plus_ms, t - tp - d)'),
+    "stdp_truncates": ("return (int32_t)llround(value);", "return (int32_t)value;"),
+    "inh_targets_any": ('*target_out = col * npc + scale_draw(r[0], ne);',
+                        '*target_out = col * npc + scale_draw(r[0], npc);'),
+    "self_excl_strict": ("if (tl >= local) tl += 1;", "if (tl > local) tl += 1;"),
+    "pct_ceil": ('uint32_t end = (uint32_t)(((uint64_t)m * acc) / 100u);',
+                 'uint32_t end = (uint32_t)(((uint64_t)m * acc + 99u) / 100u);'),
+    "ring2_member_order": ("{1, -1, 1, -1}", "{1, 1, -1, -1}"),
+    "thal_domain0": ("draw(c, (uint32_t)t, col, 1u, k, r);", "draw(c, (uint32_t)t, col, 0u, k, r);"),
+    "floor_div_truncates": ("if ((x % 65536) != 0 && x < 0) q -= 1;", ";"),
+    "l_exc_not_counted": ("s->l_exc += s->in_off[post + 1] - s->in_off[post];", ";"),
+    "e_exc_all": ("        s->e_exc++;\n", "        ;\n"),
+    "f64_u_relax_c": ("uu = uu + a * (b * vv - uu);", "uu = uu + a * (b * vv - c);"),
+    "f64_one_substep": ('for (int half = 0; half < 2; ++half)\n        vv = vv',
+                        'for (int half = 0; half < 1; ++half)\n        vv = vv'),
+    "wrap_no_neg": ("return r < 0 ? r + n : r;", "return r < 0 ? 0 : r;"),
+    "exc_delay_zero_based": ('*delay_out = 1 + scale_draw(r[1], c->max_delay_ms);',
+                             '*delay_out = scale_draw(r[1], c->max_delay_ms) + (r[1] & 1);'),
+    "key_halves_swapped": ('uint32_t key[2] = {(uint32_t)(c->seed & 0xffffffffu), (uint32_t)(c->seed >> 32)};',
+                           'uint32_t key[2] = {(uint32_t)(c->seed >> 32), (uint32_t)(c->seed & 0xffffffffu)};'),
+    "thal_amp_once_per_col": ('for (uint32_t k = 0; k < c->thal_per_col_per_ms; ++k)\n            s->cur',
+                              'for (uint32_t k = 0; k < 1; ++k)\n            s->cur'),
+    "incoming_count_includes_inhibitory": (
+        "if (!is_exc(s, p)) continue;\n"
+        "        for (int64_t k = s->row_off[p]; k < s->row_off[p + 1]; ++k) count[",
+        "for (int64_t k = s->row_off[p]; k < s->row_off[p + 1]; ++k) count["),
 }
 
 

@@ -186,6 +186,29 @@ def test_stdp_single_pair_closed_form(orc, d):
         assert sd == expect, (d, lag, sd, expect)
 
 
+def test_stdp_pair_rule_takes_each_branch_constants(orc):
+    # The pair rule of Sec. 2 ("Synaptic update") has its own amplitude and
+    # time constant on each side of t = 0.  With A+ = 0.2, tau+ = 10 ms and
+    # A- = 0.05, tau- = 30 ms every lag must match the 40-digit closed form of
+    # its own branch, rounded to Q16 with halves away from zero.
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 40
+    d = 5
+    cfg = dict(_pair_config(d), a_plus_mv=0.2, tau_plus_ms=10.0, a_minus_mv=0.05, tau_minus_ms=30.0)
+    t_pre = 60
+    for lag in range(-40, 41):
+        t_post = t_pre + d + lag
+        o = _forced(orc, cfg, _pair_network(d), [t_pre], [t_post], max(t_pre + d, t_post) + 3)
+        sd = int(o.synapses()["sd"][0])
+        if lag >= 0:
+            x = mpmath.mpf("0.2") * mpmath.e ** (-mpmath.mpf(lag) / 10) * 65536
+            expect = int(mpmath.floor(x + mpmath.mpf("0.5")))
+        else:
+            x = mpmath.mpf("0.05") * mpmath.e ** (mpmath.mpf(lag) / 30) * 65536
+            expect = -int(mpmath.floor(x + mpmath.mpf("0.5")))
+        assert sd == expect, (lag, sd, expect)
+
+
 def _nearest_pairs_bruteforce(pre, post, d, ltp, ltd):
     """Nearest-neighbour pairing by enumeration of every (pre, post) pair."""
     total = 0
