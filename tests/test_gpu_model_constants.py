@@ -1,8 +1,11 @@
-"""Parity with the oracle when the two sides of the STDP pair rule (Sec. 2,
-"Synaptic update") take different amplitudes and time constants, and when a
-depression amount no longer fits the 15 bits in which the dense pass and the
-column-staged delivery stage it (the engine then keeps to the event-driven,
-column-ordered delivery).  Bar: bit-exact, as in test_gpu_parity.py."""
+"""Parity with the oracle away from the benchmark's model constants: the two
+sides of the STDP pair rule (Sec. 2, "Synaptic update") with different
+amplitudes and time constants; a depression amount too wide for the 15 bits in
+which the dense pass and the column-staged delivery stage it (the engine then
+keeps to the event-driven, column-ordered delivery); several thalamic events
+per column per ms with another amplitude (Sec. 2, thalamic stimulus) and a
+long-term update (Table 2) with another period, bias, decay and weight bound.
+Bar: bit-exact, as in test_gpu_parity.py."""
 import pytest
 
 import workloads
@@ -46,3 +49,20 @@ def test_wide_depression_amounts_keep_to_the_ordered_delivery(eng, orc, mode):
         n.run(1100)
         assert_same_run(o, n)
         assert n.profile()["dense_steps"] == 0
+
+
+@pytest.mark.parametrize("mode", ["auto", "sparse", "staged", "dense"])
+def test_drive_and_long_term_constants_bitexact(eng, orc, mode):
+    # 3 thalamic events of 20 mV per column per ms (Philox counters
+    # (t, col, 1, k), k = 0..2); long-term update every 250 ms with bias 1000,
+    # decay 50000/65536 and wmax 6.5 mV, which about a tenth of the
+    # excitatory weights reach by 1.1 s
+    cfg = _cfg(43, thal_per_col_per_ms=3, thal_amp_q16=20 * 65536, deriv_period_ms=250,
+               deriv_bias_q16=1000, deriv_decay_q16=50000, wmax_q16=425984)
+    o = orc.Oracle(cfg)
+    o.run(1100)
+    with gpu_net(eng, cfg, mode) as n:
+        n.run(1100)
+        assert_same_run(o, n)
+        w, _ = n.weights()
+        assert (w == 425984).sum() > 1000
