@@ -1,8 +1,11 @@
 """The C-ABI library builds, loads and exports every symbol include/snn.h
-declares; host-side argument checks answer without a GPU."""
+declares; the ctypes mirrors of its structs (and of the oracle's) match the
+compiled headers field by field; host-side argument checks answer without a
+GPU."""
 import ctypes
 import os
 import re
+import subprocess
 
 import numpy as np
 import pytest
@@ -46,6 +49,43 @@ def test_config_struct_layout_matches_header():
     assert ctypes.sizeof(snn.SnnProfile) == 120
 
 
+def _compiled_layout(tmp_path, include_dir, header, structs):
+    """sizeof and offsetof of every field of the ctypes mirrors in `structs`
+    ({C type name: ctypes class}), printed by a C program built against the
+    header itself."""
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "%s"' % header, 'int main(void) {']
+    for cname, py in structs.items():
+        lines.append('printf("%s %%zu\\n", sizeof(%s));' % (cname, cname))
+        for field, _ in py._fields_:
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (cname, field, cname, field))
+    lines += ['return 0;', '}']
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", include_dir, "-o", str(exe), str(src)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout
+    return dict(line.split() for line in out.splitlines())
+
+
+def _assert_layout(got, structs):
+    for cname, py in structs.items():
+        assert int(got[cname]) == ctypes.sizeof(py), cname
+        for field, _ in py._fields_:
+            assert int(got["%s.%s" % (cname, field)]) == getattr(py, field).offset, (cname, field)
+
+
+def test_every_struct_field_matches_the_compiled_header(tmp_path):
+    structs = {"snn_config": snn.SnnConfig, "snn_spike": snn.SnnSpike, "snn_stimulus": snn.SnnStimulus,
+               "snn_counters": snn.SnnCounters, "snn_launch": snn.SnnLaunch, "snn_profile": snn.SnnProfile}
+    _assert_layout(_compiled_layout(tmp_path, os.path.join(ROOT, "include"), "snn.h", structs), structs)
+
+
+def test_oracle_binding_matches_its_header(tmp_path):
+    import oracle
+    structs = {"orc_config": oracle.OrcConfig, "orc_stim": oracle.OrcStim}
+    _assert_layout(_compiled_layout(tmp_path, os.path.join(ROOT, "oracle"), "oracle.h", structs), structs)
+
+
 def _rc_build(cfg, budget=0):
     lib = snn.load()
     h = ctypes.c_void_p()
@@ -72,7 +112,7 @@ def test_budget_is_checked_before_any_device_work():
 
 def test_strerror_covers_every_code():
     lib = snn.load()
-    for code in (0, -1, -2, -3, -4, -5, -6, -7):
+    for code in (0, -1, -2, -3, -4, -5, -6, -7, -8):
         assert lib.snn_strerror(code) and lib.snn_strerror(code) != b"unknown error"
     assert lib.snn_strerror(-99) == b"unknown error"
 
