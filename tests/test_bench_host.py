@@ -1,0 +1,98 @@
+"""Host-side pieces of bench.py that need no GPU: the committed DRAM traffic
+follows the kernel's source digest, the clock samples are summarised as the
+JSON line reports them, and the reference arm prints its line (rank 0 only)
+with the keys the line must carry."""
+import io
+import json
+import os
+import sys
+import types
+from contextlib import redirect_stdout
+
+import pytest
+
+from conftest import ROOT
+
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def test_committed_traffic_follows_the_source_digest(monkeypatch):
+    p = os.path.join(ROOT, "profiles", "k_dense_grid64_m1125_dram.json")
+    rec = json.load(open(p))
+    monkeypatch.setattr(bench, "kernel_source_digest", lambda kernel="dense": rec["source_sha256"])
+    got = bench.committed_traffic("dense", "grid64_m1125")
+    assert got == rec["dram_bytes_per_launch"]
+    # the bytes per launch are the mean of the recorded launches
+    per = [x["dram_read"] + x["dram_write"] for x in rec["launches"]]
+    assert got == pytest.approx(sum(per) / len(per), rel=1e-9)
+    monkeypatch.setattr(bench, "kernel_source_digest", lambda kernel="dense": "0" * 64)
+    assert bench.committed_traffic("dense", "grid64_m1125") is None
+    assert bench.committed_traffic("dense", "no_such_workload") is None
+
+
+def test_kernel_source_digest_tracks_the_right_files():
+    d_dense, d_step = bench.kernel_source_digest("dense"), bench.kernel_source_digest("ltp")
+    assert len(d_dense) == 64 and len(d_step) == 64 and d_dense != d_step
+    assert bench.kernel_source_digest("deliver_ordered") == d_step
+
+
+def test_clock_samples_are_summarised(tmp_path):
+    path = tmp_path / "clocks.csv"
+    path.write_text("1965, 2070, 900.1, Not Active, Not Active, Not Active, Active\n"
+                    "1980, 2070, 910.0, Not Active, Not Active, Not Active, Not Active\n"
+                    "[N/A], 2070, 0, Not Active, Not Active, Not Active, Not Active\n"
+                    "2010, 2070, 905.5, Not Active, Not Active, Not Active, Not Active\n"
+                    "truncated line\n")
+    s = bench.ClockSampler.__new__(bench.ClockSampler)
+    s.path = str(path)
+    s.f = open(os.devnull, "w")
+    s.proc = types.SimpleNamespace(terminate=lambda: None, wait=lambda timeout=None: 0, kill=lambda: None)
+    out = s.stop()
+    assert out == {"sm_mhz": 1980.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    assert not path.exists()
+
+
+def test_clock_sampler_without_nvidia_smi_reports_nothing():
+    s = bench.ClockSampler.__new__(bench.ClockSampler)
+    s.proc = None
+    assert s.stop() is None
+
+
+def _args(**kw):
+    a = dict(gpus=1, steps=5, warmup=3, impl="reference", workload=bench.DEFAULT_WORKLOAD, ref_budget_s=1.0)
+    a.update(kw)
+    return types.SimpleNamespace(**a)
+
+
+def _fake_sample(seconds, warmup_steps=0, max_steps=None):
+    return dict(value=1.5e7, unit="events/s", cores=1, kind="oracle", sample="fake sample",
+                steps=max_steps, seconds=0.5, events=7.5e6)
+
+
+def test_reference_arm_prints_one_complete_line(monkeypatch):
+    monkeypatch.setattr(bench, "oracle_sample", _fake_sample)
+    monkeypatch.setattr(bench, "dist_env", lambda: (0, 0, 1))
+    buf = io.StringIO()
+    with redirect_stdout(buf):
+        assert bench.run_reference(_args()) == 0
+    lines = buf.getvalue().strip().splitlines()
+    assert len(lines) == 1
+    line = json.loads(lines[0])
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["impl"] == "reference" and line["value"] == 1.5e7 and line["steps"] == 5
+    assert line["ms_per_step"] == pytest.approx(100.0)
+    assert line["config"]["workload"] == bench.DEFAULT_WORKLOAD
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"] == {"value": 1.5e7, "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_reference_arm_is_silent_off_rank_0(monkeypatch):
+    monkeypatch.setattr(bench, "oracle_sample", lambda *a, **k: pytest.fail("rank 1 must not run the oracle"))
+    monkeypatch.setattr(bench, "dist_env", lambda: (1, 1, 2))
+    buf = io.StringIO()
+    with redirect_stdout(buf):
+        assert bench.run_reference(_args(gpus=2)) == 0
+    assert buf.getvalue() == ""
