@@ -195,6 +195,33 @@ def committed_traffic(kernel: str, workload: str):
     return d.get("dram_bytes_per_launch")
 
 
+def deriv_updates(t0: int, t1: int, period: int) -> int:
+    """Long-term updates carried out by the launches of steps t0 .. t1 - 1: the
+    update that closes step m runs with the launch of step m + 1, so these are
+    the multiples of the period in [max(t0, 1), t1)."""
+    if period <= 0 or t1 <= t0:
+        return 0
+    below = (t0 - 1) // period if t0 >= 1 else 0
+    return (t1 - 1) // period - below
+
+
+def algorithmic_bytes(d_events, d_exc, d_ltp, n_neurons, neuron_launches, n_exc_syn, updates, dd):
+    """Algorithmic bytes moved by each kernel over the timed region, from the
+    per-unit figures: 8 B per delivered event (target + weight), 8 B per event
+    on a plastic synapse (sd read + write), 12 B per potentiation visit, 16 B
+    per plastic synapse per long-term update, 32 B per neuron per step.  The
+    work the dense pass did (dd: its own counts) is charged to it and taken
+    out of the event-driven kernels' share."""
+    return {
+        "deliver": 8.0 * (d_events - dd["dense_events"]) + 8.0 * (d_exc - dd["dense_exc_events"]),
+        "ltp": 12.0 * max(0, d_ltp - dd["dense_ltp_visits"]),
+        "neuron": 32.0 * n_neurons * neuron_launches,
+        "deriv": 16.0 * n_exc_syn * max(0, updates - dd["dense_deriv_steps"]),
+        "dense": (8.0 * dd["dense_events"] + 8.0 * dd["dense_exc_events"] + 12.0 * dd["dense_ltp_visits"]
+                  + 16.0 * n_exc_syn * dd["dense_deriv_steps"]),
+    }
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -437,22 +464,10 @@ def main():
     value = total_events / secs
     rate_hz = d_spikes / n_neurons / (K / 1000.0)
     n_exc_syn = cfg["grid_x"] * cfg["grid_y"] * cfg["exc_per_col"] * cfg["fanout"]
-    # algorithmic bytes moved by each kernel over the timed region (the
-    # per-unit figures): 8 B per delivered event (target +
-    # weight), 8 B per event on a plastic synapse (sd read + write), 12 B per
-    # potentiation visit, 16 B per plastic synapse per long-term update,
-    # 32 B per neuron per step
     dd = {k: prof1[k] - prof0[k] for k in ("dense_steps", "dense_deriv_steps", "dense_events",
                                              "dense_exc_events", "dense_ltp_visits")}
-    deriv_runs = prof["deriv"][0]
-    alg = {
-        "deliver": 8.0 * (d_events - dd["dense_events"]) + 8.0 * (d_exc - dd["dense_exc_events"]),
-        "ltp": 12.0 * max(0, d_ltp - dd["dense_ltp_visits"]),
-        "neuron": 32.0 * n_neurons * prof["neuron"][0],
-        "deriv": 16.0 * n_exc_syn * max(0, deriv_runs - dd["dense_deriv_steps"]),
-        "dense": (8.0 * dd["dense_events"] + 8.0 * dd["dense_exc_events"] + 12.0 * dd["dense_ltp_visits"]
-                  + 16.0 * n_exc_syn * dd["dense_deriv_steps"]),
-    }
+    updates = deriv_updates(c0["t"], c1["t"], cfg["deriv_period_ms"])
+    alg = algorithmic_bytes(d_events, d_exc, d_ltp, n_neurons, prof["neuron"][0], n_exc_syn, updates, dd)
     peak, peak_kind = measured_peaks()
     names = ("deliver", "neuron", "ltp", "deriv", "dense")
     kernel_ms = {k: prof[k][1] for k in names}

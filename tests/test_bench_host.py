@@ -1,7 +1,9 @@
 """Host-side pieces of bench.py that need no GPU: the committed DRAM traffic
 follows the kernel's source digest, the clock samples are summarised as the
-JSON line reports them, and the reference arm prints its line (rank 0 only)
-with the keys the line must carry."""
+JSON line reports them, the reference arm prints its line (rank 0 only)
+with the keys the line must carry, and the per-kernel algorithmic bytes
+charge each kernel the work it did (long-term updates counted per period
+closed inside the timed launches, not per launch)."""
 import io
 import json
 import os
@@ -96,3 +98,28 @@ def test_reference_arm_is_silent_off_rank_0(monkeypatch):
     with redirect_stdout(buf):
         assert bench.run_reference(_args(gpus=2)) == 0
     assert buf.getvalue() == ""
+
+
+@pytest.mark.parametrize("t0,t1,period,n", [
+    (3, 2003, 1000, 2),      # the bench's default: updates closing steps 999 and 1999
+    (0, 1000, 1000, 0),      # the update closing step 999 runs with step 1000's launch
+    (0, 1001, 1000, 1),
+    (1000, 1001, 1000, 1),
+    (1001, 2000, 1000, 0),
+    (5, 5, 1000, 0),
+    (0, 5000, 0, 0),         # no long-term plasticity
+    (0, 21, 7, 2),
+])
+def test_deriv_updates_counts_the_periods_closed_in_the_timed_launches(t0, t1, period, n):
+    assert bench.deriv_updates(t0, t1, period) == n
+
+
+def test_algorithmic_bytes_charge_each_kernel_its_own_work():
+    dd = dict(dense_steps=1, dense_deriv_steps=1, dense_events=100, dense_exc_events=60, dense_ltp_visits=50)
+    alg = bench.algorithmic_bytes(d_events=1000, d_exc=700, d_ltp=400, n_neurons=10, neuron_launches=4,
+                                  n_exc_syn=30, updates=2, dd=dd)
+    assert alg == {"deliver": 8.0 * 900 + 8.0 * 640, "ltp": 12.0 * 350, "neuron": 32.0 * 40,
+                   "deriv": 16.0 * 30 * 1, "dense": 8.0 * 100 + 8.0 * 60 + 12.0 * 50 + 16.0 * 30}
+    # a long-term update done by the dense pass is not charged to k_deriv
+    alg = bench.algorithmic_bytes(1000, 700, 400, 10, 4, 30, updates=1, dd=dd)
+    assert alg["deriv"] == 0.0
