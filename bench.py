@@ -504,7 +504,7 @@ def main():
         "raster": {"capacity": raster_cap, "dropped": c1["raster_dropped"]},
         "roofline": roofline,
         "kernels": per_kernel,
-        "gpu_launches": int(sum(prof[k][0] for k in names)),
+        "gpu_launches": int(prof1["kernels"] - prof0["kernels"]),
         "build_s": round(t_build, 2),
         "e2e": e2e,
         "small_net": small,

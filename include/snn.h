@@ -144,6 +144,9 @@ typedef struct {
     int64_t dense_events;            /* synaptic events delivered by the dense pass */
     int64_t dense_exc_events;
     int64_t dense_ltp_visits;        /* potentiation visits done by the dense pass */
+    int64_t kernels;                 /* kernels launched by the profiled steps, every kind (a
+                                        kind above may group two: k_fold + k_deriv, the
+                                        column-ordered + column-staged deliveries) */
 } snn_profile;
 
 typedef struct snn_net snn_net;

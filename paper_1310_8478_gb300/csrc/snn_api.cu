@@ -128,6 +128,7 @@ struct snn_net {
     size_t ev_used = 0;
     double prof_ms[kKinds] = {0};
     int64_t prof_n[kKinds] = {0};
+    int64_t prof_kernels = 0;       // kernels launched by the profiled steps
 };
 
 struct snn_batch {
@@ -638,7 +639,9 @@ void launch_step(snn_net *net, int32_t t, cudaStream_t s)
     // sparse grids follow the net's size (a warp per spiker / per 32 buckets)
     const int g_ltp = sized_grid(net, L.ltp_blocks_per_sm, net->N, L.ltp_block / 32);
     const int g_del = sized_grid(net, L.deliver_blocks_per_sm, (int64_t)net->N * dn.D / 4, L.deliver_block);
+    int launched = 0;
     k_ltp<<<g_ltp, L.ltp_block, 0, s>>>(dn, t_now, 0);
+    ++launched;
     mark(2);
     // long-term update when t closes a period (decided on the device, so the
     // same launches serve every step and graphs need no variants): the
@@ -647,17 +650,22 @@ void launch_step(snn_net *net, int32_t t, cudaStream_t s)
         mark(3);
         k_fold<<<sized_grid(net, 8, net->n_rin, 4096), 256, 0, s>>>(dn, t_now, 0);
         k_deriv<<<sized_grid(net, 8, (int64_t)dn.C * dn.ne, L.deriv_block / 32), L.deriv_block, 0, s>>>(dn, t_now, 0);
+        launched += 2;
         mark(3);
     }
     mark(0);
     if (dn.ordered_ok) k_deliver_ordered<<<net->ordered_grid, kOrderedBlock, 0, s>>>(dn, t_now);
     else k_deliver<<<g_del, L.deliver_block, 0, s>>>(dn, t_now);
-    if (dn.staged_ok)
+    ++launched;
+    if (dn.staged_ok) {
         k_deliver_cols<<<net->staged_grid, kStagedBlock, staged_smem_bytes(dn.npc, kStagedBlock), s>>>(dn, t_now);
+        ++launched;
+    }
     mark(0);
     if (net->dense_ok) {
         mark(4);
         k_dense<<<net->dense_grid, L.dense_block, dense_smem_bytes(dn.npc, L.dense_block), s>>>(dn, t_now);
+        ++launched;
         mark(4);
     }
     // [S2(t) S3(t)]
@@ -666,8 +674,13 @@ void launch_step(snn_net *net, int32_t t, cudaStream_t s)
     mark(1);
     if (dn.vd) k_neuron_f64<<<nb_neuron, L.neuron_block, 0, s>>>(dn, t_now, t_next);
     else k_neuron_f32<<<nb_neuron, L.neuron_block, 0, s>>>(dn, t_now, t_next);
-    if (dn.probe_n) k_probe<<<(dn.probe_n + 255) / 256, 256, 0, s>>>(dn, t_now);
+    ++launched;
+    if (dn.probe_n) {
+        k_probe<<<(dn.probe_n + 255) / 256, 256, 0, s>>>(dn, t_now);
+        ++launched;
+    }
     mark(1);
+    if (prof) net->prof_kernels += launched;
 }
 
 uint32_t effective_graph_len(const snn_net *net)
@@ -1667,6 +1680,7 @@ int snn_set_profile(snn_net *net, int on)
     if (!net) { set_error("net is NULL"); return SNN_EINVAL; }
     net->profile = on != 0;
     for (int k = 0; k < kKinds; ++k) { net->prof_ms[k] = 0; net->prof_n[k] = 0; }
+    net->prof_kernels = 0;
     net->ev_used = 0;
     return SNN_OK;
 }
@@ -1678,6 +1692,7 @@ int snn_read_profile(snn_net *net, snn_profile *out)
         out->launches[k] = net->prof_n[k];
         out->ms[k] = net->prof_ms[k];
     }
+    out->kernels = net->prof_kernels;
     DevCounters hc{};
     SNN_TRY(read_counters_raw(net, &hc));
     out->dense_steps = (int64_t)hc.dense_steps;

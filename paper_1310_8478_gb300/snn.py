@@ -74,7 +74,7 @@ class SnnProfile(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64 * 5), ("ms", ctypes.c_double * 5),
                 ("dense_steps", ctypes.c_int64), ("dense_deriv_steps", ctypes.c_int64),
                 ("dense_events", ctypes.c_int64), ("dense_exc_events", ctypes.c_int64),
-                ("dense_ltp_visits", ctypes.c_int64)]
+                ("dense_ltp_visits", ctypes.c_int64), ("kernels", ctypes.c_int64)]
 
 
 SPIKE_DTYPE = np.dtype([("t", np.int32), ("gid", np.int32)])
@@ -408,7 +408,8 @@ class Network:
         p = SnnProfile()
         _check(self._lib.snn_read_profile(self.h, ctypes.byref(p)), "snn_read_profile")
         out = {k: (int(p.launches[i]), float(p.ms[i])) for i, k in enumerate(KERNELS)}
-        for k in ("dense_steps", "dense_deriv_steps", "dense_events", "dense_exc_events", "dense_ltp_visits"):
+        for k in ("dense_steps", "dense_deriv_steps", "dense_events", "dense_exc_events", "dense_ltp_visits",
+                  "kernels"):
             out[k] = int(getattr(p, k))
         return out
 

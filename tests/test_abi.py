@@ -46,7 +46,7 @@ def test_config_struct_layout_matches_header():
     assert ctypes.sizeof(c) == 136
     assert ctypes.sizeof(snn.SnnCounters) == 64
     assert ctypes.sizeof(snn.SnnLaunch) == 44
-    assert ctypes.sizeof(snn.SnnProfile) == 120
+    assert ctypes.sizeof(snn.SnnProfile) == 128
 
 
 def _compiled_layout(tmp_path, include_dir, header, structs):
