@@ -83,7 +83,8 @@ typedef struct {
     uint32_t deriv_period_ms;            /* long-term update period; 0 = never */
     int32_t deriv_bias_q16;              /* added to w at each update */
     int32_t deriv_decay_q16;             /* sd = (sd * decay + 2^15) >> 16 */
-    uint32_t thal_per_col_per_ms;        /* thalamic events per column per ms */
+    uint32_t thal_per_col_per_ms;        /* thalamic events per column per ms (times the
+                                            columns: at most 2^31 - 1) */
     int32_t thal_amp_q16;                /* current of one thalamic event */
     uint64_t seed;                       /* key of the Philox4x32-10 draws */
     uint32_t flags;                      /* SNN_STDP_OFF | SNN_DELIVERY_OFF | SNN_FP64 */

@@ -240,6 +240,11 @@ int check_config(const snn_config *c)
     if (c->reserved != 0) { set_error("reserved field must be 0"); return SNN_EINVAL; }
     if (c->flags & ~(SNN_STDP_OFF | SNN_DELIVERY_OFF | SNN_FP64)) { set_error("unknown flags"); return SNN_EINVAL; }
     if (c->deriv_period_ms > 0x3fffffffu) { set_error("deriv_period_ms too large"); return SNN_EINVAL; }
+    // the drive enumerates the events of a step with 32-bit indices
+    if ((uint64_t)c->grid_x * c->grid_y * c->thal_per_col_per_ms > 0x7fffffffull) {
+        set_error("more than 2^31 - 1 thalamic events per ms");
+        return SNN_EINVAL;
+    }
     return SNN_OK;
 }
 

@@ -97,6 +97,7 @@ def _rc_build(cfg, budget=0):
     dict(grid_x=0), dict(neurons_per_col=1), dict(exc_per_col=0), dict(fanout=0), dict(fanout=70000),
     dict(pct_ring=(40, 30, 20, 11)), dict(max_delay_ms=0), dict(max_delay_ms=32), dict(wmax_q16=-1),
     dict(tau_plus_ms=0.0), dict(a_minus_mv=-0.1), dict(flags=8),
+    dict(grid_x=2, thal_per_col_per_ms=1 << 30),
 ])
 def test_bad_config_is_rejected_before_any_device_work(bad):
     rc, h = _rc_build(workloads.custom(**bad))
