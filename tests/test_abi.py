@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 import workloads
-from conftest import ROOT
+from conftest import ROOT, build_readme_c_example
 
 import paper_1310_8478_gb300 as eng
 from paper_1310_8478_gb300 import snn
@@ -132,3 +132,42 @@ def test_compact_target_slot_decode_is_exact():
         assert r < 2 ** 32
         v = np.arange(13 * npc, dtype=np.uint64)
         assert np.array_equal((v * r) >> np.uint64(32), v // np.uint64(npc)), npc
+
+
+def test_readme_c_example_builds_and_fails_loudly_without_a_gpu(tmp_path):
+    # the README's plain-C program compiles warning-free against the header
+    # and links against the library; on a machine without a GPU the first
+    # call reports a CUDA error and the program exits 1 (there is no CPU path)
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present: tests/test_zz_readme_example.py runs the program")
+    exe = build_readme_c_example(tmp_path, eng.build_engine())
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 1
+    assert "CUDA" in r.stderr and r.stdout == ""
+
+
+def test_readme_c_example_configures_the_one_column_workload():
+    # every "c.field = value;" of the README program, evaluated, equals the
+    # col1_m100 workload (the GPU test compares the program's output with the
+    # oracle on that workload)
+    text = open(os.path.join(ROOT, "README.md")).read()
+    code = re.search(r"```c\n(.*?)```", text, re.S).group(1)
+    got = {}
+    for field, idx, expr in re.findall(r"\bc\.(\w+)(?:\[(\d)\])?\s*=\s*([^;]+);", code):
+        value = eval(expr, {})
+        if idx:
+            got.setdefault(field, [0, 0, 0, 0])[int(idx)] = value
+        else:
+            got[field] = value
+    cfg = workloads.workload("col1_m100")
+    want = snn.make_config(cfg)
+    for field, _ in snn.SnnConfig._fields_:
+        if field in ("reserved", "flags"):
+            continue
+        if field == "pct_ring":
+            assert got["pct_ring"] == list(cfg["pct_ring"])
+        elif field == "raster_capacity":
+            assert got[field] > 0
+        else:
+            assert got[field] == getattr(want, field), field
