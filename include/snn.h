@@ -285,8 +285,8 @@ int snn_read_neurons_f64(snn_net *net, uint32_t first, uint32_t count, double *h
 
 /*
  * snn_set_probe -- membrane traces of chosen neurons (Sec. 2 "Production of
- * observables": the trace of the membrane potential and other state
- * variables of individual neurons can be activated; Fig. 2-3): from the next
+ * observables", which offers optional recording of v and the other state
+ * variables of selected neurons; Fig. 2-3): from the next
  * step on, v and u of host_gids[0..n) after every step's update are kept on
  * the device for up to max_steps steps.  n = 0 switches the probe off.
  * SNN_EINVAL for a gid out of range.

@@ -2,9 +2,8 @@
 //
 // Sec. 2 of the paper ("Initial construction of the connectivity
 // infrastructure", "Distributed generation of reproducible connections"):
-// each neuron's forward synapses are generated from global ids only, grouped
-// by delay ("the list of local synapses is further divided in sets according
-// to the value of the axo-synaptic delay"), and every target learns its
+// each neuron's forward synapses are generated from global ids only, kept
+// in one bucket per axonal delay value, and every target learns its
 // incoming synapses.  On one GPU the MPI handshake becomes a device-side
 // in-degree count, a prefix sum and a scatter into the reverse index.
 #include "snn_internal.cuh"

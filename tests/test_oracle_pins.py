@@ -350,8 +350,8 @@ def test_benchmark_mix_counts_and_delays(orc):
 
 
 def test_single_column_projects_to_itself(orc):
-    # Sec. 2: "in the case of a single column, all synapses are projected by
-    # the column to itself", whatever the mix.
+    # Sec. 2: a network of one column sends every synapse back into that
+    # column, whatever the projection mix.
     cfg = workloads.custom(grid_x=1, grid_y=1, fanout=300, pct_ring=(40, 30, 20, 10), seed=9)
     o = orc.Oracle(cfg)
     s = o.synapses()
