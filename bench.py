@@ -54,6 +54,8 @@ def parse_args():
     ap.add_argument("--serve-bench", type=int, default=0, metavar="REQUESTS",
                     help="instead: the serving workload (Poisson arrivals) with this many requests")
     ap.add_argument("--serve-rate", type=float, default=200.0, help="mean arrivals per second")
+    ap.add_argument("--serve-requests", type=int, default=24,
+                    help="requests of the serving leg of the default line (0: no serving leg)")
     return ap.parse_args()
 
 
@@ -294,16 +296,16 @@ def run_batch_bench(args):
     return 0
 
 
-def run_serve_bench(args):
-    """Simulation requests arriving as a Poisson stream (mean --serve-rate per
+SERVE_WORKLOAD = ("Poisson requests, grid side log-uniform 1..32, M in {100, 400, 1125}, "
+                  "duration uniform 100..5000 ms, seeds 5000..")
+
+
+def serve_leg(n_requests: int, rate: float, budget_gb: float, stream):
+    """Simulation requests arriving as a Poisson stream (mean `rate` per
     second; grid side log-uniform 1..32, M in {100, 400, 1125}, duration
     uniform 100..5000 ms, seeds 5000..) served with continuous batching under
-    the --batch-budget-gb device budget; latency = completion - arrival."""
-    import torch
-    import paper_1310_8478_gb300 as eng
+    a device budget of `budget_gb`; latency = completion - arrival."""
     from paper_1310_8478_gb300 import serve
-    torch.cuda.set_device(0)
-    eng.build_engine()
     params = {}
 
     def cfg_of(i, rng):
@@ -311,21 +313,29 @@ def run_serve_bench(args):
         params[i] = d
         return c
 
-    reqs = serve.poisson_requests(args.serve_bench, args.serve_rate, cfg_of, lambda i, rng: params[i])
+    reqs = serve.poisson_requests(n_requests, rate, cfg_of, lambda i, rng: params[i])
+    srv = serve.Server(int(budget_gb * 1e9), chunk_ms=10, stream=stream)
+    t0 = time.perf_counter()
+    res = srv.serve(reqs)
+    wall = time.perf_counter() - t0
+    ev = sum(r.events for r in res)
+    return {"requests": len(res), "rate_per_s": rate, "budget_gb": budget_gb,
+            "value": ev / wall, "unit": "events/s", "wall_s": wall, "events": ev,
+            "latency": serve.latency_stats(res), "chunks": srv.chunks, "rebatches": srv.rebatches,
+            "sim_ms_total": int(sum(r.steps for r in res))}
+
+
+def run_serve_bench(args):
+    """The serving workload alone (see serve_leg), --serve-bench requests."""
+    import torch
+    import paper_1310_8478_gb300 as eng
+    torch.cuda.set_device(0)
+    eng.build_engine()
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
-        srv = serve.Server(int(args.batch_budget_gb * 1e9), chunk_ms=10, stream=stream)
-        t0 = time.perf_counter()
-        res = srv.serve(reqs)
-        wall = time.perf_counter() - t0
-    ev = sum(r.events for r in res)
-    line = {"metric": "synaptic events/s", "mode": "serve", "unit": "events/s", "n_gpus": 1,
-            "requests": len(res), "rate_per_s": args.serve_rate, "budget_gb": args.batch_budget_gb,
-            "config": {"workload": "Poisson requests, grid side log-uniform 1..32, M in {100, 400, 1125}, "
-                                   "duration uniform 100..5000 ms, seeds 5000.."},
-            "value": ev / wall, "wall_s": wall, "events": ev, "latency": serve.latency_stats(res),
-            "chunks": srv.chunks, "rebatches": srv.rebatches,
-            "sim_ms_total": int(sum(r.steps for r in res))}
+        leg = serve_leg(args.serve_bench, args.serve_rate, args.batch_budget_gb, stream)
+    line = {"metric": "synaptic events/s", "mode": "serve", "n_gpus": 1, "config": {"workload": SERVE_WORKLOAD}}
+    line.update(leg)
     print(json.dumps(line), flush=True)
     return 0
 
@@ -452,6 +462,17 @@ def main():
                          "us_per_step": round(1000.0 * a0.elapsed_time(a1) / 1000.0, 2),
                          "graph_steps": sn.get_launch()["graph_steps"]}
 
+        # serving: p50 / p99 latency and throughput of a Poisson request
+        # stream under continuous batching, after the main net is released;
+        # a failure here is reported in the line instead of losing it
+        served = None
+        if args.serve_requests > 0 and rank == 0:
+            try:
+                served = {"workload": SERVE_WORKLOAD}
+                served.update(serve_leg(args.serve_requests, args.serve_rate, args.batch_budget_gb, stream))
+            except Exception as e:  # noqa: BLE001
+                served = {"error": "%s: %s" % (type(e).__name__, e)}
+
     d_events = c1["e_all"] - c0["e_all"]
     d_exc = c1["e_exc"] - c0["e_exc"]
     d_ltp = c1["l_exc"] - c0["l_exc"]
@@ -508,6 +529,7 @@ def main():
         "build_s": round(t_build, 2),
         "e2e": e2e,
         "small_net": small,
+        "serve": served,
         "cpu_baseline": None if cpu is None else {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")},
         "clocks": clk,
     }

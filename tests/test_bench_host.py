@@ -123,3 +123,18 @@ def test_algorithmic_bytes_charge_each_kernel_its_own_work():
     # a long-term update done by the dense pass is not charged to k_deriv
     alg = bench.algorithmic_bytes(1000, 700, 400, 10, 4, 30, updates=1, dd=dd)
     assert alg["deriv"] == 0.0
+
+
+def test_serving_leg_reports_latency_and_throughput(monkeypatch):
+    # the serving leg of the default line, driven by the fake engine of
+    # test_serve_host.py (host logic only; the GPU run is the bench's own)
+    import test_serve_host as ts
+    from paper_1310_8478_gb300 import serve
+    monkeypatch.setattr(serve, "snn", types.SimpleNamespace(Network=ts.FakeNet, Batch=ts.FakeBatch,
+                                                            SnnError=ts.FakeError, ENOMEM=ts.ENOMEM))
+    ts.FakeNet.live.clear()
+    leg = bench.serve_leg(6, 200.0, 150.0, None)
+    assert leg["requests"] == 6 and leg["unit"] == "events/s" and leg["value"] > 0
+    assert set(leg["latency"]) == {"p50_s", "p99_s", "mean_s", "max_s"}
+    assert leg["latency"]["p50_s"] <= leg["latency"]["p99_s"] <= leg["latency"]["max_s"]
+    assert leg["sim_ms_total"] >= 6 * 100 and not ts.FakeNet.live
