@@ -3,7 +3,9 @@ follows the kernel's source digest, the clock samples are summarised as the
 JSON line reports them, the reference arm prints its line (rank 0 only)
 with the keys the line must carry, and the per-kernel algorithmic bytes
 charge each kernel the work it did (long-term updates counted per period
-closed inside the timed launches, not per launch)."""
+closed inside the timed launches, not per launch).  bench.main runs end to
+end against a fake engine and fake CUDA calls, and its line carries every key
+of the contract."""
 import io
 import json
 import os
@@ -138,3 +140,120 @@ def test_serving_leg_reports_latency_and_throughput(monkeypatch):
     assert set(leg["latency"]) == {"p50_s", "p99_s", "mean_s", "max_s"}
     assert leg["latency"]["p50_s"] <= leg["latency"]["p99_s"] <= leg["latency"]["max_s"]
     assert leg["sim_ms_total"] >= 6 * 100 and not ts.FakeNet.live
+
+
+class _FakeBenchNet:
+    """Stands in for snn.Network in bench.main: fixed work per step, no device."""
+
+    def __init__(self, cfg, stream=None, raster_capacity=0, **kw):
+        self.n = cfg["grid_x"] * cfg["grid_y"] * cfg["neurons_per_col"]
+        self.device_bytes = self.n * 100
+        self.t = 0
+        self.prof_on = False
+        self.prof_steps = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def run(self, n):
+        self.t += n
+        if self.prof_on:
+            self.prof_steps += n
+
+    def run_host_counts(self, n, events):
+        assert len(events) > 0
+        self.run(n)
+
+    def set_profile(self, on):
+        self.prof_on = bool(on)
+        self.prof_steps = 0
+
+    def profile(self):
+        k = self.prof_steps
+        out = {"deliver": (k, 0.1 * k), "neuron": (k, 0.05 * k), "ltp": (k, 0.02 * k),
+               "deriv": (k, 0.01 * k), "dense": (k, 1.0 * k)}
+        out.update(dense_steps=k // 2, dense_deriv_steps=0, dense_events=1000 * k, dense_exc_events=800 * k,
+                   dense_ltp_visits=500 * k, kernels=7 * k)
+        return out
+
+    def counters(self):
+        return {"t": self.t, "spikes": 10 * self.t, "e_all": 2000 * self.t, "e_exc": 1500 * self.t,
+                "l_exc": 900 * self.t, "raster_dropped": 0}
+
+    def reset(self):
+        self.t = 0
+
+    def set_thalamic(self, on):
+        pass
+
+    def raster_reset(self):
+        pass
+
+    def get_launch(self):
+        return {"graph_steps": 50}
+
+    def close(self):
+        pass
+
+
+def test_main_line_carries_every_key_with_a_fake_engine(monkeypatch, capsys):
+    # bench.main end to end on the CPU: a fake engine and fake CUDA calls
+    # stand in for the device; the line must parse and carry every key of
+    # the contract, with the arithmetic of its derived figures
+    import contextlib
+
+    import torch
+
+    import paper_1310_8478_gb300 as pkg
+    import test_serve_host as ts
+    from paper_1310_8478_gb300 import serve
+
+    class Ev:
+        def __init__(self, **kw):
+            pass
+
+        def record(self, stream=None):
+            pass
+
+        def elapsed_time(self, other):
+            return 5.0 * 4.0                       # 4 ms per step over the 5 timed steps
+
+    cuda = types.SimpleNamespace(is_available=lambda: True, set_device=lambda i: None,
+                                 mem_get_info=lambda: (280e9, 285e9),
+                                 Stream=lambda: types.SimpleNamespace(cuda_stream=0),
+                                 stream=lambda s: contextlib.nullcontext(), synchronize=lambda: None, Event=Ev)
+    monkeypatch.setattr(torch, "cuda", cuda)
+    real_empty = torch.empty
+    monkeypatch.setattr(torch, "empty", lambda *a, pin_memory=False, **k: real_empty(*a, **k))
+    monkeypatch.setattr(pkg, "Network", _FakeBenchNet)
+    monkeypatch.setattr(pkg, "build_engine", lambda *a, **k: None)
+    monkeypatch.setattr(serve, "snn", types.SimpleNamespace(Network=ts.FakeNet, Batch=ts.FakeBatch,
+                                                            SnnError=ts.FakeError, ENOMEM=ts.ENOMEM))
+    ts.FakeNet.live.clear()
+    monkeypatch.setattr(bench, "oracle_sample", lambda seconds: _fake_sample(seconds, max_steps=7))
+    monkeypatch.setattr(bench, "dist_env", lambda: (0, 0, 1))
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--steps", "5", "--warmup", "3", "--serve-requests", "4"])
+    assert bench.main() == 0
+    lines = [ln for ln in capsys.readouterr().out.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    line = json.loads(lines[0])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "roofline", "cpu_baseline", "e2e",
+                "gpu_launches", "clocks", "serve"):
+        assert key in line, key
+    assert line["steps"] == 5 and line["warmup"] == 3 and line["n_gpus"] == 1
+    assert line["ms_per_step"] == pytest.approx(4.0)
+    assert line["value"] == pytest.approx(2000 * 5 / 0.020)
+    assert line["gpu_launches"] == 35
+    assert line["config"]["workload"].startswith(bench.DEFAULT_WORKLOAD)
+    r = line["roofline"]
+    assert r["kernel"] == "dense" and r["bound"] == "hbm" and r["unit"] == "GB/s"
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"], rel=1e-3)
+    assert set(line["e2e"]) >= {"value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step"}
+    assert line["e2e"]["h2d_bytes_per_step"] == 64 * 64 * 12      # one 12-byte event per column and step
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    assert line["serve"]["requests"] == 4 and "p99_s" in line["serve"]["latency"]
+    assert line["kernels"]["deriv"]["alg_gbs"] == 0.0                # no period closes in steps 3..7
