@@ -4,6 +4,10 @@ TEST INFRASTRUCTURE, NOT PRODUCT CODE.  Only tests/, the smoke check in
 __graft_entry__ and the cpu_baseline / reference leg of bench.py may import
 this package.  It does not import the CUDA path and the CUDA path does not
 import it; both take the plain parameter dictionaries of workloads.py.
+
+Every function of oracle.c is pinned against the paper and the mathematics
+by tests/test_oracle_pins.py and tests/test_oracle_generator_pins.py (their
+sensitivity: tests/test_oracle_mutants.py); none is "parity unpinned".
 """
 from __future__ import annotations
 
