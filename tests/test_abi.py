@@ -171,3 +171,24 @@ def test_readme_c_example_configures_the_one_column_workload():
             assert got[field] > 0
         else:
             assert got[field] == getattr(want, field), field
+
+
+@pytest.mark.parametrize("cfg", [
+    workloads.custom(grid_x=3, grid_y=2, seed=77),
+    workloads.custom(grid_x=2, grid_y=2, neurons_per_col=997, exc_per_col=800, thal_per_col_per_ms=3,
+                     thal_amp_q16=7 * 65536, seed=(1 << 40) + 12345),
+])
+def test_host_thalamic_events_equal_the_oracle(orc, cfg):
+    # snn_thalamic_events is host code of the library (no GPU): every event it
+    # lists -- step, target and amount -- equals the oracle's draw for that
+    # (step, column, k), in step order, at the start and far into a run
+    C = cfg["grid_x"] * cfg["grid_y"]
+    K = cfg["thal_per_col_per_ms"]
+    for t0, n_ms in ((0, 5), (123456, 3)):
+        ev = snn.snn_thalamic_events(cfg, t0, n_ms)
+        assert len(ev) == n_ms * C * K
+        assert np.all(np.diff(ev["t"]) >= 0) and ev["t"][0] == t0 and ev["t"][-1] == t0 + n_ms - 1
+        assert np.all(ev["q16"] == cfg["thal_amp_q16"])
+        want = sorted((t, orc.thalamic_target(cfg, t, col, k))
+                      for t in range(t0, t0 + n_ms) for col in range(C) for k in range(K))
+        assert sorted(zip(ev["t"].tolist(), ev["gid"].tolist())) == want
