@@ -73,6 +73,18 @@ MUTANTS = {
         "if (!is_exc(s, p)) continue;\n"
         "        for (int64_t k = s->row_off[p]; k < s->row_off[p + 1]; ++k) count[",
         "for (int64_t k = s->row_off[p]; k < s->row_off[p + 1]; ++k) count["),
+    # operation order of the neuron update (the bit-exact sequence)
+    "f32_minus_u_plus_i_swapped": ("        x = x - uu;\n        x = x + cur;", "        x = x + cur;\n        x = x - uu;"),
+    "f32_quadratic_not_horner": ("        x = 0.04f * vv;\n        x = x + 5.0f;\n        x = x * vv;",
+                                 "        x = vv * vv;\n        x = 0.04f * x;\n        x = x + 5.0f * vv;"),
+    # (where the factor 0.5 of the half step is applied is not observable:
+    # scaling by a power of two commutes with rounding in the normal range)
+    "f32_rest_constant_folded_with_u": ("        x = x + 140.0f;\n        x = x - uu;",
+                                        "        x = x + (140.0f - uu);"),
+    "f32_u_step_distributed": ("    x = x - uu;\n    x = a * x;\n    uu = uu + x;",
+                               "    x = a * x;\n    x = x - a * uu;\n    uu = uu + x;"),
+    "f64_minus_u_plus_i_swapped": ("140.0 - uu + cur)", "140.0 + cur - uu)"),
+    "f64_quadratic_not_horner": ("((0.04 * vv + 5.0) * vv + 140.0", "(0.04 * (vv * vv) + 5.0 * vv + 140.0"),
 }
 
 

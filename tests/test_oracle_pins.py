@@ -537,3 +537,154 @@ def test_threshold_is_inclusive(orc):
             break
     assert found >= 1, "no state reaching exactly 30 mV was found"
     assert below >= 1, "no state reaching the float32 just below 30 mV was found"
+
+
+# ---------------------------------------------------------------------------
+# The neuron update bit for bit (reading of Sec. 2 "Spiking neuron model" and
+# the 0.5 ms membrane step of Sec. 3): v takes two Euler half steps with the
+# same u and I, each written as the operations
+#     x = 0.04 v; x += 5; x *= v; x += 140; x -= u; x += I; x *= 0.5; v += x
+# then u one 1 ms step  y = b v; y -= u; y *= a; u += y,  then the threshold
+# v >= 30 -> v = c, u += d; I = (float) Iq * 2^-16.  Every operation is one
+# correctly rounded IEEE-754 operation (no fused multiply-add).  The expected
+# values below come from an exact model of IEEE-754 round-to-nearest-even
+# written here on rational numbers (no floating-point hardware involved), and,
+# for many more states, from numpy scalar-type arithmetic in the same order.
+# ---------------------------------------------------------------------------
+from fractions import Fraction  # noqa: E402
+
+_F32 = (24, -126)          # significand bits, minimum normal exponent
+_F64 = (53, -1022)
+
+
+def _ieee_round(q: Fraction, fmt) -> Fraction:
+    """q rounded to the nearest value of the binary format (ties to even)."""
+    p, emin = fmt
+    if q == 0:
+        return Fraction(0)
+    a = abs(q)
+    e = a.numerator.bit_length() - a.denominator.bit_length()
+    if Fraction(2) ** e > a:
+        e -= 1
+    e = max(e, emin)
+    ulp = Fraction(2) ** (e - (p - 1))
+    m = a / ulp
+    n = m.numerator // m.denominator
+    r = m - n
+    if r > Fraction(1, 2) or (r == Fraction(1, 2) and n % 2 == 1):
+        n += 1
+    return (n * ulp) if q > 0 else -(n * ulp)
+
+
+def _neuron_exact(v, u, iq, excitatory, fmt):
+    """One neuron step on exact rationals with one rounding per operation."""
+    R = lambda x: _ieee_round(x, fmt)  # noqa: E731
+    a = R(Fraction(2, 100) if excitatory else Fraction(1, 10))
+    b = R(Fraction(2, 10))
+    c = Fraction(-65)
+    d = Fraction(8 if excitatory else 2)
+    k004, half = R(Fraction(4, 100)), Fraction(1, 2)
+    cur = R(R(Fraction(iq)) * Fraction(1, 65536))
+    v, u = Fraction(v), Fraction(u)
+    for _ in range(2):
+        x = R(k004 * v)
+        x = R(x + 5)
+        x = R(x * v)
+        x = R(x + 140)
+        x = R(x - u)
+        x = R(x + cur)
+        x = R(half * x)
+        v = R(v + x)
+    y = R(b * v)
+    y = R(y - u)
+    y = R(a * y)
+    u = R(u + y)
+    if v >= 30:
+        return c, R(u + d), True
+    return v, u, False
+
+
+def _neuron_numpy(v, u, iq, excitatory, dtype):
+    """The same sequence on numpy arrays of one scalar type (per-op rounding)."""
+    f = dtype
+    a = np.where(excitatory, f(0.02), f(0.1)).astype(f)
+    d = np.where(excitatory, f(8.0), f(2.0)).astype(f)
+    cur = (iq.astype(f) * f(2.0 ** -16)).astype(f)
+    v = v.astype(f)
+    u = u.astype(f)
+    for _ in range(2):
+        x = f(0.04) * v
+        x = x + f(5.0)
+        x = x * v
+        x = x + f(140.0)
+        x = x - u
+        x = x + cur
+        x = f(0.5) * x
+        v = v + x
+    y = f(0.2) * v
+    y = y - u
+    y = a * y
+    u = u + y
+    fired = v >= f(30.0)
+    return np.where(fired, f(-65.0), v).astype(f), np.where(fired, u + d, u).astype(f), fired
+
+
+def _random_states(n, seed):
+    # v in [-90, 35] mV, u in [-20, 10], I in [-50, 60] mV as Q16, both kinds;
+    # a quarter of the states start close to the firing threshold crossing
+    rng = np.random.default_rng(seed)
+    v = rng.uniform(-90.0, 35.0, n)
+    v[: n // 4] = rng.uniform(-55.0, -40.0, n // 4)
+    u = rng.uniform(-20.0, 10.0, n)
+    iq = rng.integers(-50 * 65536, 60 * 65536, n).astype(np.int32)
+    exc = rng.integers(0, 2, n).astype(bool)
+    return v, u, iq, exc
+
+
+def _oracle_steps(orc, v, u, iq, exc, fp64):
+    out_v = np.empty(len(v), np.float64 if fp64 else np.float32)
+    out_u = np.empty_like(out_v)
+    out_f = np.empty(len(v), bool)
+    for i in range(len(v)):
+        out_v[i], out_u[i], out_f[i] = orc.neuron_step(v[i], u[i], int(iq[i]), bool(exc[i]), fp64)
+    return out_v, out_u, out_f
+
+
+@pytest.mark.parametrize("fp64", [False, True])
+def test_neuron_sequence_bit_exact_on_exact_rounding_model(orc, fp64):
+    fmt = _F64 if fp64 else _F32
+    v, u, iq, exc = _random_states(1500, 11 + fp64)
+    dt = np.float64 if fp64 else np.float32
+    v, u = v.astype(dt), u.astype(dt)
+    ov, ou, of = _oracle_steps(orc, v, u, iq, exc, fp64)
+    fired = 0
+    for i in range(len(v)):
+        ev, eu, ef = _neuron_exact(float(v[i]), float(u[i]), int(iq[i]), bool(exc[i]), fmt)
+        assert (bool(of[i]), Fraction(float(ov[i])), Fraction(float(ou[i]))) == (ef, ev, eu), (
+            i, float(v[i]), float(u[i]), int(iq[i]), bool(exc[i]))
+        fired += ef
+    assert 100 < fired < len(v) - 100      # both branches of the threshold are exercised
+
+
+@pytest.mark.parametrize("fp64", [False, True])
+def test_neuron_sequence_bit_exact_on_many_states(orc, fp64):
+    dt = np.float64 if fp64 else np.float32
+    v, u, iq, exc = _random_states(100_000, 21 + fp64)
+    v, u = v.astype(dt), u.astype(dt)
+    ev, eu, ef = _neuron_numpy(v, u, iq, exc, dt)
+    ov, ou, of = _oracle_steps(orc, v, u, iq, exc, fp64)
+    assert np.array_equal(of, ef)
+    assert np.array_equal(ov.view(np.uint64 if fp64 else np.uint32), ev.view(np.uint64 if fp64 else np.uint32))
+    assert np.array_equal(ou.view(np.uint64 if fp64 else np.uint32), eu.view(np.uint64 if fp64 else np.uint32))
+
+
+def test_exact_rounding_model_matches_known_float32_values():
+    # the rational model itself: nearest float32 of 0.1 is 13421773 * 2^-27,
+    # of 0.04 is 10737418 * 2^-28, ties go to the even significand, and
+    # 1 + 2^-24 (a tie) rounds down to 1 while 1 + 3 * 2^-24 rounds up
+    assert _ieee_round(Fraction(1, 10), _F32) == Fraction(13421773, 2 ** 27)
+    assert _ieee_round(Fraction(4, 100), _F32) == Fraction(10737418, 2 ** 28)
+    assert _ieee_round(1 + Fraction(1, 2 ** 24), _F32) == 1
+    assert _ieee_round(1 + Fraction(3, 2 ** 24), _F32) == 1 + Fraction(2, 2 ** 23)
+    assert _ieee_round(Fraction(1, 10), _F64) == Fraction(3602879701896397, 2 ** 55)
+    assert _ieee_round(Fraction(-3, 2 ** 150), _F32) == -Fraction(2, 2 ** 149)
