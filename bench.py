@@ -29,10 +29,10 @@ sys.path.insert(0, ROOT)
 import workloads  # noqa: E402
 
 DEFAULT_WORKLOAD = "grid64_m1125"
-# the oracle's bounded sample: same column model and mix on the 8x8 torus,
-# steps [26, 26 + n) (onset of the dense regime), single core
-CPU_SAMPLE_WORKLOAD = "grid8_m1125"
-CPU_SAMPLE_SKIP_MS = 26
+# the oracle's bounded sample: the same column model, fan-out and projection
+# mix on the 16x16 torus (the 64x64 net does not fit a bounded CPU sample),
+# over the same simulated steps as the GPU's timed region, single core
+CPU_SAMPLE_WORKLOAD = "grid16_m1125"
 
 
 def parse_args():
@@ -54,6 +54,10 @@ def parse_args():
     ap.add_argument("--serve-bench", type=int, default=0, metavar="REQUESTS",
                     help="instead: the serving workload (Poisson arrivals) with this many requests")
     ap.add_argument("--serve-rate", type=float, default=200.0, help="mean arrivals per second")
+    ap.add_argument("--no-atomics", dest="atomics", action="store_false",
+                    help="skip the L2-reduction / gather / shared-atomic microbenchmark")
+    ap.add_argument("--no-steady", dest="steady", action="store_false",
+                    help="skip the dense-regime and period-end legs after the timed region")
     ap.add_argument("--serve-requests", type=int, default=24,
                     help="requests of the serving leg of the default line (0: no serving leg)")
     return ap.parse_args()
@@ -80,26 +84,28 @@ def dist_env():
 # ---------------------------------------------------------------------------
 # the oracle's bounded sample (cpu_baseline leg and the reference arm)
 # ---------------------------------------------------------------------------
-def oracle_sample(seconds: float, warmup_steps: int = 0, max_steps: int | None = None):
+def oracle_sample(seconds: float, t0: int, t1: int):
+    """The oracle on the CPU sample workload, timed over steps [t0, t1) (the
+    GPU leg's window) or until `seconds` have passed, whichever comes first;
+    construction and the steps before t0 are not timed."""
     import oracle
     cfg = workloads.workload(CPU_SAMPLE_WORKLOAD)
     sim = oracle.Oracle(cfg)
-    sim.run(max(0, CPU_SAMPLE_SKIP_MS - warmup_steps))
-    sim.run(warmup_steps)
+    sim.run(t0)
     c0 = sim.counters()
-    t0 = time.perf_counter()
+    t_start = time.perf_counter()
     steps = 0
-    while True:
+    while t0 + steps < t1:
         sim.run(1)
         steps += 1
-        el = time.perf_counter() - t0
-        if el >= seconds or (max_steps is not None and steps >= max_steps):
+        if time.perf_counter() - t_start >= seconds:
             break
+    el = time.perf_counter() - t_start
     c1 = sim.counters()
     ev = c1["e_all"] - c0["e_all"]
-    sample = ("oracle on the %s torus (same column model, fan-out and mix), steps %d..%d of its run "
-              "(onset of the dense regime), 1 thread" % (
-                  "8x8", CPU_SAMPLE_SKIP_MS, CPU_SAMPLE_SKIP_MS + steps - 1))
+    sample = ("oracle on the %dx%d torus (%s: same column model, fan-out and mix), steps %d..%d of its run "
+              "(the GPU leg's timed steps), 1 thread" % (
+                  cfg["grid_x"], cfg["grid_y"], CPU_SAMPLE_WORKLOAD, t0, t0 + steps - 1))
     return dict(value=ev / el, unit="events/s", cores=1, kind="oracle", sample=sample,
                 steps=steps, seconds=el, events=ev)
 
@@ -108,14 +114,15 @@ def run_reference(args):
     rank, _, world = dist_env()
     if rank != 0:
         return 0
-    r = oracle_sample(args.ref_budget_s, warmup_steps=args.warmup, max_steps=args.steps)
+    r = oracle_sample(args.ref_budget_s, args.warmup, args.warmup + args.steps)
     cfg = workloads.workload(args.workload)
     line = {
         "impl": "reference", "metric": "synaptic events/s", "value": r["value"], "unit": "events/s",
         "n_gpus": args.gpus, "steps": r["steps"], "warmup": args.warmup,
         "ms_per_step": 1000.0 * r["seconds"] / max(1, r["steps"]), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "i32/f32", "data": "synthetic",
-        "config": {"workload": args.workload, "stands_in": "8x8 torus of the same column model (CPU bound)",
+        "config": {"workload": args.workload,
+                   "stands_in": "%s torus of the same column model, same steps (CPU bound)" % CPU_SAMPLE_WORKLOAD,
                    "grid": [cfg["grid_x"], cfg["grid_y"]], "fanout": cfg["fanout"]},
         "cpu_baseline": {"value": r["value"], "unit": "events/s", "cores": 1, "kind": "oracle",
                          "sample": r["sample"]},
@@ -367,7 +374,8 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        cpu = oracle_sample(args.cpu_seconds)      # before any GPU work; same process, no fork
+        # before any GPU work; same process, no fork
+        cpu = oracle_sample(args.cpu_seconds, args.warmup, args.warmup + args.steps)
 
     # rank 0 compiles whatever is stale; the other ranks then find it built
     if rank == 0:
@@ -411,6 +419,7 @@ def main():
         prof = net.profile()
         prof1 = prof
         net.set_profile(False)
+        device_digest = raster_digest(net, W, W + K) if c1["raster_dropped"] == 0 else None
 
         # end-to-end leg: the same workload restarted, driven from host memory
         # (the thalamic events of every step are copied in from pinned host
@@ -440,9 +449,28 @@ def main():
             e2e = {"value": (ce1["e_all"] - ce0["e_all"]) / el, "unit": "events/s",
                    "h2d_bytes_per_step": per_step * snn.STIM_DTYPE.itemsize,
                    "d2h_bytes_per_step": 3 * ctypes_sizeof_counters(), "steps": KE,
-                   "bitexact_with_device_run": bool(ce1["e_all"] - ce0["e_all"] == c1["e_all"] - c0["e_all"]
-                                                    and KE == K)}
+                   "same_events_as_device_run": bool(ce1["e_all"] - ce0["e_all"] == c1["e_all"] - c0["e_all"]
+                                                     and KE == K)}
+            if KE == K and device_digest is not None and ce1["raster_dropped"] == 0:
+                e2e["raster_sha256_equals_device_run"] = raster_digest(net, W, W + K) == device_digest
+            net.set_thalamic(True)
+
+        # the regime that dominates the workload's first simulated second (the
+        # net runs away to nearly every neuron firing every step, so the dense
+        # pass takes the steps) and a step that closes a plasticity period
+        steady = None
+        if args.steady and rank == 0:
+            steady = steady_leg(net, cfg, stream, n_neurons, args)
         net.close()
+
+        # the rates of scattered L2 reductions, gathers and shared atomics on
+        # an array the size of the net's input array: the roof of the
+        # event-driven delivery, which is bound by them rather than by HBM
+        atomics = None
+        if rank == 0 and args.atomics:
+            clk_a = ClockSampler(local_rank)
+            atomics = snn.snn_microbench_atomics(n_neurons * 4, 4096, stream)
+            atomics["clocks"] = clk_a.stop()
 
         # the 1-column, M = 100 workload is launch/latency bound: its figure is
         # microseconds per step with CUDA-graph replays (50 steps per graph)
@@ -508,6 +536,16 @@ def main():
         dram = traffic * dd["dense_steps"] / (kernel_ms[dom] / 1000.0) / 1e9
         roofline["dram_achieved"] = round(dram, 1)
         roofline["dram_frac"] = round(dram / peak, 4)
+    if atomics is not None and prof["deliver"][1] > 0:
+        # events delivered by the event-driven kernels per second of their
+        # time, against the measured rate of scattered L2 reductions (one per
+        # event on another column) and of shared atomics (own column)
+        ev_sparse = d_events - dd["dense_events"]
+        roofline["atomic"] = {"kernel": "deliver", "events_per_s": round(ev_sparse / (prof["deliver"][1] / 1e3)),
+                              "red_global_window_per_s": round(atomics["red_global_window_gops"] * 1e9),
+                              "atom_shared_window_per_s": round(atomics["atom_shared_window_gops"] * 1e9),
+                              "frac_of_l2_reductions": round(ev_sparse / (prof["deliver"][1] / 1e3)
+                                                             / (atomics["red_global_window_gops"] * 1e9), 4)}
     line = {
         "metric": "synaptic events/s", "value": value, "unit": "events/s", "n_gpus": world, "steps": K,
         "warmup": W, "ms_per_step": ms / K, "higher_is_better": True,
@@ -528,6 +566,8 @@ def main():
         "gpu_launches": int(prof1["kernels"] - prof0["kernels"]),
         "build_s": round(t_build, 2),
         "e2e": e2e,
+        "steady": steady,
+        "atomics": atomics,
         "small_net": small,
         "serve": served,
         "cpu_baseline": None if cpu is None else {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")},
@@ -535,6 +575,76 @@ def main():
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def raster_digest(net, t0: int, t1: int) -> str:
+    """sha256 of the raster of steps [t0, t1) as little-endian int32 (t, gid)
+    pairs sorted by (t, gid)."""
+    import hashlib
+    import numpy as np
+    t, g = net.raster(t0, t1)
+    return hashlib.sha256(np.stack([t, g], axis=1).astype("<i4").tobytes()).hexdigest()
+
+
+def fused_dense_bytes(cfg) -> float:
+    """Bytes one dense step must move by the fused pass's own count: every
+    synapse's 2-byte target, and on excitatory rows the weight (4 B) and the
+    derivative's read and write (8 B)."""
+    s_all = workloads.n_synapses(cfg)
+    s_exc = cfg["grid_x"] * cfg["grid_y"] * cfg["exc_per_col"] * cfg["fanout"]
+    return 2.0 * s_all + 12.0 * s_exc
+
+
+def timed_window(net, stream, n_steps: int, device: int = 0):
+    """n_steps steps with per-kernel profiling, CUDA events and sampled clocks."""
+    import torch
+    net.set_profile(True)
+    p0, c0 = net.profile(), net.counters()
+    clocks = ClockSampler(device)
+    torch.cuda.synchronize()
+    a0 = torch.cuda.Event(enable_timing=True)
+    a1 = torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    net.run(n_steps)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    p1, c1 = net.profile(), net.counters()
+    net.set_profile(False)
+    return a0.elapsed_time(a1), p0, p1, c0, c1, clk
+
+
+def steady_leg(net, cfg, stream, n_neurons, args, dense_at: int = 60, n_dense: int = 10, period_from: int = 995,
+               n_period: int = 10):
+    """After the timed region: n_dense steps from step dense_at (the run-away
+    regime, dense pass), and n_period steps from period_from (they cross the
+    long-term update that closes step period - 1)."""
+    peak, peak_kind = measured_peaks()
+    out = {}
+    for name, start, steps in (("dense_regime", dense_at, n_dense), ("period_end", period_from, n_period)):
+        t = net.t
+        if t > start:
+            continue
+        if start > t:
+            net.run(start - t)
+        ms, p0, p1, c0, c1, clk = timed_window(net, stream, steps)
+        ev = c1["e_all"] - c0["e_all"]
+        spikes = c1["spikes"] - c0["spikes"]
+        rate = spikes / n_neurons / (steps / 1000.0)
+        dense_steps = p1["dense_steps"] - p0["dense_steps"]
+        dense_ms = p1["dense"][1] - p0["dense"][1]
+        leg = {"steps": [start, start + steps], "ms_per_step": ms / steps, "value": ev / (ms / 1000.0),
+               "unit": "events/s", "rate_hz": rate,
+               "wall_s_per_sim_s_per_hz": (ms / 1000.0 / (steps / 1000.0)) / rate if rate > 0 else None,
+               "dense_steps": dense_steps, "clocks": clk,
+               "kernel_ms": {k: round(p1[k][1] - p0[k][1], 3) for k in ("deliver", "neuron", "ltp", "deriv", "dense")}}
+        if dense_steps > 0 and dense_ms > 0:
+            fused = fused_dense_bytes(cfg) * dense_steps
+            ach = fused / (dense_ms / 1000.0) / 1e9
+            leg["dense_fused"] = {"bytes_per_step": fused_dense_bytes(cfg), "achieved": round(ach, 1), "peak": peak,
+                                  "peak_kind": peak_kind, "unit": "GB/s", "frac": round(ach / peak, 4)}
+        out[name] = leg
+    return out
 
 
 def ctypes_sizeof_counters():

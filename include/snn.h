@@ -115,8 +115,9 @@ typedef struct {
  * Zero fields keep the current value.
  */
 typedef struct {
-    uint32_t deliver_block;          /* threads per block of the event-driven delivery (multiple of 32) */
-    uint32_t deliver_blocks_per_sm;
+    uint32_t deliver_block;          /* threads per block of the event-driven delivery (multiple of 32;
+                                        the column-ordered delivery gives one column to each block) */
+    uint32_t deliver_blocks_per_sm;  /* resident blocks per SM of the event-driven delivery (at most) */
     uint32_t neuron_block;           /* threads per block of the neuron update */
     uint32_t ltp_block;              /* threads per block of the event-driven potentiation */
     uint32_t ltp_blocks_per_sm;
@@ -131,8 +132,9 @@ typedef struct {
                                         through shared memory when its expected events (spikes of
                                         the last max_delay steps x fan-out / max_delay, plus
                                         inhibitory spikes of the step before x fan-out) reach this
-                                        many per 1000 neurons; 0xffffffff = never (the default
-                                        for nets of fewer than 16 columns, else 30000) */
+                                        many per 1000 neurons; 0xffffffff = never (the default:
+                                        the column-ordered delivery, which stages the source
+                                        column's own neurons, is faster on the measured nets) */
 } snn_launch;
 
 /* Per-kernel device time collected while profiling is on (CUDA events), and
@@ -377,6 +379,38 @@ int snn_reset(snn_net *net);
  */
 int snn_thalamic_events(const snn_config *cfg, int32_t t0, uint32_t n_ms, snn_stimulus *host_events,
                         size_t cap, size_t *n_out);
+
+/*
+ * snn_microbench_atomics -- measurement only: the rates (10^9 operations per
+ * second) of the memory operations the event-driven delivery and
+ * potentiation are built from, at the access patterns they use (Sec. 2
+ * steps 2.4-2.6: every synaptic event adds its weight into the target's Q16
+ * input and reads the target's last spike; Table 2 rows "axonal spikes ->
+ * synaptic spikes" and "currents + LTD").  On an int32 array of array_bytes
+ * (the size of a net's input array), ops_per_thread operations per thread of
+ * one resident wave, each timed once after a warm-up with CUDA events on
+ * cuda_stream (NULL: the legacy default stream):
+ *   red_global_random   red.global.add.s32 at uniformly random words
+ *   red_global_window   the same inside one 1250-word window per warp (one
+ *                       column's inputs), the window moving every 64 ops
+ *   red_global_coalesced 32 consecutive words per warp instruction
+ *   ld_global_random    4-byte loads at uniformly random words (L2 gathers)
+ *   atom_shared_window  shared-memory atomicAdd at random words of 1250
+ * Allocates array_bytes of device memory with cudaMalloc for the call.
+ * Errors: SNN_EINVAL (array below 10 000 bytes or above 16 GiB, no ops),
+ * SNN_ENOMEM, SNN_ECUDA.
+ */
+typedef struct {
+    double red_global_random_gops;
+    double red_global_window_gops;
+    double red_global_coalesced_gops;
+    double ld_global_random_gops;
+    double atom_shared_window_gops;
+    double array_bytes;
+    double threads;
+} snn_atomic_rates;
+int snn_microbench_atomics(size_t array_bytes, uint32_t ops_per_thread, void *cuda_stream,
+                           snn_atomic_rates *out);
 
 /* snn_free -- release the handle and its device memory (NULL is allowed). */
 void snn_free(snn_net *net);

@@ -23,7 +23,7 @@ LIB_PATH = os.path.join(BUILD_DIR, "libsnn.so")
 # the access is skipped
 CHECKED_DIR = os.path.join(BUILD_DIR, "checked")
 CHECKED_LIB_PATH = os.path.join(BUILD_DIR, "libsnn_checked.so")
-SOURCES = ["snn_build.cu", "snn_step.cu", "snn_dense.cu", "snn_api.cu"]
+SOURCES = ["snn_build.cu", "snn_step.cu", "snn_dense.cu", "snn_api.cu", "snn_microbench.cu"]
 HEADERS = ["snn_internal.cuh"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -102,6 +102,7 @@ struct snn_net {
     uint8_t *canon_delay = nullptr;
     int64_t *rin_off = nullptr;
     uint64_t *rin = nullptr;
+    uint32_t *rin32 = nullptr;
     DevCounters *ctr = nullptr;
     int32_t *lut = nullptr;
     int64_t raster_steps_cap = 0;   // entries of dn.raster_step_off
@@ -287,6 +288,21 @@ int sized_grid(const snn_net *net, uint32_t blocks_per_sm, int64_t units, int64_
     return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)grid_for(net, blocks_per_sm)));
 }
 
+// whether the reverse index takes 4-byte entries: compact targets and rows of
+// at most kRin32MaxRow stored slots
+bool rin32_ok(const snn_config *c, bool explicit_net)
+{
+    const uint32_t m_store = (c->fanout + 7u) & ~7u;
+    return !explicit_net && c->neurons_per_col >= kMinCompactNpc && c->neurons_per_col <= kMaxCompactNpc &&
+           m_store <= kRin32MaxRow;
+}
+
+bool rin32_ok(const snn_net *net)
+{
+    return net->tgt16 != nullptr && net->dn.uniform_m != 0 && net->dn.uniform_m <= kRin32MaxRow &&
+           rin32_ok(&net->cfg, net->explicit_net);
+}
+
 // footprint of everything but the raster (bytes)
 size_t footprint(const snn_config *c, uint32_t N, int64_t S, int64_t n_rin, bool explicit_net)
 {
@@ -297,7 +313,7 @@ size_t footprint(const snn_config *c, uint32_t N, int64_t S, int64_t n_rin, bool
     b += (size_t)c->grid_x * c->grid_y * kSlotStride * 4;                                  // neighbour table
     b += (size_t)N * kDoffStride * 2;             // delay offsets
     b += ((size_t)N + 1) * 8 * 2;                 // row_off, rin_off
-    b += (size_t)n_rin * 12;                      // reverse index + its LTP accumulator
+    b += (size_t)n_rin * (rin32_ok(c, explicit_net) ? 8 : 12);   // reverse index + its LTP accumulator
     b += (size_t)N * 24;                          // v u I (hist, last_old) last_spike
     if (c->flags & SNN_FP64) b += (size_t)N * 16; // v u in double
     b += D * N * 4 + D * 8;                       // ring
@@ -404,8 +420,14 @@ int setup_dense(snn_net *net)
     net->dn.ordered_ok = 0;
     if (!net->tgt16) return SNN_OK;
     {
+        // the column-ordered delivery: deliver_block threads per column, at
+        // most deliver_blocks_per_sm resident blocks per SM (one wave)
         int per_sm = 0;
-        SNN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_deliver_ordered, (int)kOrderedBlock, 0));
+        const uint32_t ob = net->launch.deliver_block;
+        const size_t obytes = ordered_smem_bytes(net->cfg.neurons_per_col, ob);
+        SNN_CUDA(cudaFuncSetAttribute(k_deliver_ordered, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)obytes));
+        SNN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_deliver_ordered, (int)ob, obytes));
+        per_sm = std::min<int>(per_sm, (int)std::max(1u, net->launch.deliver_blocks_per_sm));
         if (per_sm >= 1) {
             net->dn.ordered_ok = 1;
             net->ordered_grid = (int)std::min<int64_t>(net->dn.C, (int64_t)per_sm * net->sm_count);
@@ -503,12 +525,19 @@ int finish_build(snn_net *net)
     SNN_CUDA(cudaMemcpyAsync(&n_rin, net->rin_off + N, 8, cudaMemcpyDeviceToHost, s));
     SNN_CUDA(cudaStreamSynchronize(s));
     net->n_rin = n_rin;
-    SNN_TRY(dalloc_t(net, (size_t)std::max<int64_t>(n_rin, 1), &net->rin));
+    // 4-byte entries where the source fits the compact packing and the row
+    // position 11 bits, else 8-byte entries
+    if (rin32_ok(net)) {
+        SNN_TRY(dalloc_t(net, (size_t)std::max<int64_t>(n_rin, 1), &net->rin32));
+    } else {
+        SNN_TRY(dalloc_t(net, (size_t)std::max<int64_t>(n_rin, 1), &net->rin));
+    }
     dn.rin = net->rin;
+    dn.rin32 = net->rin32;
     SNN_TRY(dalloc_t(net, (size_t)std::max<int64_t>(n_rin, 1), &dn.sd_rev));
     SNN_CUDA(cudaMemsetAsync(dn.sd_rev, 0, (size_t)std::max<int64_t>(n_rin, 1) * 4, s));
     dn.n_rin = n_rin;
-    k_fill_reverse<<<g, 256, 0, s>>>(dn, cursor, net->rin);
+    k_fill_reverse<<<g, 256, 0, s>>>(dn, cursor, net->rin, net->rin32);
     SNN_CUDA(cudaGetLastError());
     SNN_CUDA(cudaStreamSynchronize(s));
     dfree(net, indeg_exc);
@@ -558,9 +587,11 @@ int start_net(const snn_config *cfg, void *cuda_stream, size_t budget, snn_net *
     net->launch.dense_block = 512;
     net->launch.dense_rows = 0;
     net->launch.dense_permille = 250;
-    // column staging pays from about 30 events per neuron and step on nets of
-    // distinct neighbour columns; smaller tori default to never (no launch)
-    net->launch.staged_permille = cfg->grid_x * cfg->grid_y >= 16 ? 30000u : 0xffffffffu;
+    // the 13-column staging no longer pays against the column-ordered
+    // delivery, which stages the source column's own neurons (measured on the
+    // 64x64 M = 1125 onset and the 128x128 paper geometry): off by default
+    // (no launch); a launch shape can still ask for it
+    net->launch.staged_permille = 0xffffffffu;
     (void)cuda_stream;
     return SNN_OK;
 }
@@ -627,7 +658,10 @@ void launch_flush(snn_net *net)
     cudaMemcpyAsync(&net->ctr->ltp_pending, &none, sizeof none, cudaMemcpyHostToDevice, s);
 }
 
-void launch_step(snn_net *net, int32_t t, cudaStream_t s)
+// exact_t: t is the step itself (an eager launch), not only its parity (a
+// launch captured into a graph that serves many chunks of steps); the host
+// then leaves out the long-term update's kernels in steps that close no period
+void launch_step(snn_net *net, int32_t t, cudaStream_t s, bool exact_t)
 {
     const DevNet &dn = net->dn;
     const int *t_now = &net->ctr->t_slot[t & 1];
@@ -651,7 +685,7 @@ void launch_step(snn_net *net, int32_t t, cudaStream_t s)
     // long-term update when t closes a period (decided on the device, so the
     // same launches serve every step and graphs need no variants): the
     // event-driven LTP is folded into sd first, both passes read sd afterwards
-    if (P) {
+    if (P && (!exact_t || (t > 0 && (uint32_t)t % P == 0))) {
         mark(3);
         k_fold<<<sized_grid(net, 8, net->n_rin, 4096), 256, 0, s>>>(dn, t_now, 0);
         k_deriv<<<sized_grid(net, 8, (int64_t)dn.C * dn.ne, L.deriv_block / 32), L.deriv_block, 0, s>>>(dn, t_now, 0);
@@ -659,7 +693,9 @@ void launch_step(snn_net *net, int32_t t, cudaStream_t s)
         mark(3);
     }
     mark(0);
-    if (dn.ordered_ok) k_deliver_ordered<<<net->ordered_grid, kOrderedBlock, 0, s>>>(dn, t_now);
+    if (dn.ordered_ok)
+        k_deliver_ordered<<<net->ordered_grid, L.deliver_block, ordered_smem_bytes(dn.npc, L.deliver_block), s>>>(dn,
+                                                                                                           t_now);
     else k_deliver<<<g_del, L.deliver_block, 0, s>>>(dn, t_now);
     ++launched;
     if (dn.staged_ok) {
@@ -701,7 +737,7 @@ int build_graph(snn_net *net, uint32_t L)
 {
     cudaGraph_t g = nullptr;
     SNN_CUDA(cudaStreamBeginCapture(net->stream, cudaStreamCaptureModeThreadLocal));
-    for (uint32_t k = 0; k < L; ++k) launch_step(net, (int32_t)k, net->stream);
+    for (uint32_t k = 0; k < L; ++k) launch_step(net, (int32_t)k, net->stream, false);
     cudaError_t e = cudaStreamEndCapture(net->stream, &g);
     if (e != cudaSuccess) {
         set_error("graph capture failed: %s", cudaGetErrorString(e));
@@ -770,7 +806,7 @@ int run_steps(snn_net *net, uint32_t n_ms)
             left -= L;
             net->ltp_owed = true;
         } else {
-            launch_step(net, t, net->stream);
+            launch_step(net, t, net->stream, true);
             SNN_CUDA(cudaGetLastError());
             net->t += 1;
             left -= 1;
@@ -1245,13 +1281,13 @@ namespace {
 // the next `count` steps of every net (from its own t), each net on its own
 // branch stream, joined back into the batch's main stream (captured into a
 // graph, or run eagerly)
-void batch_enqueue(snn_batch *b, uint32_t count)
+void batch_enqueue(snn_batch *b, uint32_t count, bool exact_t)
 {
     cudaEventRecord(b->fork, b->main);
     for (size_t i = 0; i < b->nets.size(); ++i) {
         snn_net *n = b->nets[i];
         cudaStreamWaitEvent(b->branch[i], b->fork, 0);
-        for (uint32_t k = 0; k < count; ++k) launch_step(n, n->t + (int32_t)k, b->branch[i]);
+        for (uint32_t k = 0; k < count; ++k) launch_step(n, n->t + (int32_t)k, b->branch[i], exact_t);
         cudaEventRecord(b->join[i], b->branch[i]);
         cudaStreamWaitEvent(b->main, b->join[i], 0);
     }
@@ -1265,7 +1301,7 @@ int batch_capture(snn_batch *b)
     }
     cudaGraph_t g = nullptr;
     SNN_CUDA(cudaStreamBeginCapture(b->main, cudaStreamCaptureModeThreadLocal));
-    batch_enqueue(b, b->L);
+    batch_enqueue(b, b->L, false);
     cudaError_t e = cudaStreamEndCapture(b->main, &g);
     if (e != cudaSuccess) { set_error("batch capture failed: %s", cudaGetErrorString(e)); return SNN_ECUDA; }
     e = cudaGraphInstantiate(&b->graph, g, 0);
@@ -1309,7 +1345,7 @@ int snn_batch_run(snn_batch *b, uint32_t n_ms)
             for (snn_net *n : b->nets) n->t += (int32_t)L;
             left -= L;
         } else {
-            batch_enqueue(b, 1);
+            batch_enqueue(b, 1, true);
             SNN_CUDA(cudaGetLastError());
             for (snn_net *n : b->nets) n->t += 1;
             left -= 1;

@@ -173,8 +173,9 @@ __global__ void k_scan_write(const int32_t *in, uint32_t n, const long long *blo
 }
 
 // Warp per excitatory source row: append every synapse to its target's
-// incoming list (order inside a list is irrelevant: LTP only adds integers).
-__global__ void k_fill_reverse(DevNet n, int32_t *cursor, uint64_t *rin)
+// incoming list (order inside a list is irrelevant: LTP only adds integers),
+// as a 4-byte entry (rin32) or an 8-byte one (rin).
+__global__ void k_fill_reverse(DevNet n, int32_t *cursor, uint64_t *rin, uint32_t *rin32)
 {
     const int lane = threadIdx.x & 31;
     const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
@@ -188,7 +189,12 @@ __global__ void k_fill_reverse(DevNet n, int32_t *cursor, uint64_t *rin)
             for (uint32_t k = lo + lane; k < hi; k += 32) {
                 const uint32_t t = target_gid(n, col, base + k);
                 const int slot = atomicAdd(&cursor[t], 1);
-                rin[n.rin_off[t] + slot] = (uint64_t)p | ((uint64_t)k << 32) | ((uint64_t)d << 48);
+                if (rin32) {
+                    const uint32_t sl = __umulhi((uint32_t)n.tgt16[base + k], n.npc_recip);
+                    rin32[n.rin_off[t] + slot] = rin32_entry(inverse_slot(sl), n.npc, p % n.npc, d, k);
+                } else {
+                    rin[n.rin_off[t] + slot] = (uint64_t)p | ((uint64_t)k << 32) | ((uint64_t)d << 48);
+                }
             }
         }
     }

@@ -63,7 +63,9 @@ struct DevNet {
     const int32_t *nbr;              // [C][kSlotStride] global column of every slot
     int32_t *w, *sd;                 // [S] weight, STDP derivative; rows sorted by delay
     const int64_t *rin_off;          // [N + 1] reverse index (incoming excitatory synapses)
-    const uint64_t *rin;             // source | ordinal-in-row << 32 | delay << 48
+    const uint64_t *rin;             // source | ordinal-in-row << 32 | delay << 48, or NULL
+    const uint32_t *rin32;           // nets with compact targets and rows of at most 2048 slots:
+                                     // 4-byte entries (rin32_entry), or NULL
     int32_t *sd_rev;                 // [n_rin] LTP of the event-driven pass, accumulated in
                                      //         reverse-index order (contiguous per target);
                                      //         folded into sd before every long-term update
@@ -210,6 +212,27 @@ __host__ __device__ __forceinline__ void gen_synapse(const GenParams &g, uint32_
         tl = draw_below(r.x, g.npc);
     }
     target = tcol * g.npc + tl;
+}
+
+// the slot of the opposite column offset: the column of slot s seen from
+// the target's side (ring 1 and 3 members come in +/- pairs, ring 2 members
+// pair with their diagonal opposite)
+__host__ __device__ __forceinline__ uint32_t inverse_slot(uint32_t slot)
+{
+    if (slot == 0) return 0;
+    const uint32_t ring = (slot - 1) / 4, member = (slot - 1) & 3u;
+    return 1 + 4 * ring + (ring == 1 ? 3u - member : member ^ 1u);
+}
+
+// 4-byte reverse entry: bits 0..15 the source as inverse_slot * npc + local
+// id (the same packing as the compact forward targets, relative to the
+// target's column), bits 16..20 the delay, bits 21..31 the synapse's position
+// in the stored source row
+constexpr uint32_t kRin32MaxRow = 2048;
+__host__ __device__ __forceinline__ uint32_t rin32_entry(uint32_t inv_slot, uint32_t npc, uint32_t local, uint32_t d,
+                                                         uint32_t pos)
+{
+    return (inv_slot * npc + local) | (d << 16) | (pos << 21);
 }
 
 // target gid of synapse k whose source lives in column src_col
@@ -364,7 +387,7 @@ __global__ void k_count_indeg(DevNet n, int32_t *indeg_exc, int32_t *indeg_inh);
 __global__ void k_scan_sums(const int32_t *in, uint32_t n, long long *block_sums);
 __global__ void k_scan_carry(long long *block_sums, uint32_t n_blocks);
 __global__ void k_scan_write(const int32_t *in, uint32_t n, const long long *block_sums, int64_t *out);
-__global__ void k_fill_reverse(DevNet n, int32_t *cursor, uint64_t *rin);
+__global__ void k_fill_reverse(DevNet n, int32_t *cursor, uint64_t *rin, uint32_t *rin32);
 __global__ void k_max2(const int32_t *a, const int32_t *b, uint32_t n, int32_t *out2);
 __global__ void k_init_state(DevNet n);
 __global__ void k_reset_weights(DevNet n, int32_t w_exc0, int32_t w_inh0);
@@ -385,7 +408,7 @@ __global__ void k_fold(DevNet n, const int *t_now, int force);
 
 size_t dense_smem_bytes(uint32_t npc, uint32_t block);
 size_t staged_smem_bytes(uint32_t npc, uint32_t block);
+size_t ordered_smem_bytes(uint32_t npc, uint32_t block);
 constexpr uint32_t kStagedBlock = 512;      // threads per block of the column-staged delivery
-constexpr uint32_t kOrderedBlock = 256;     // threads per block of the column-ordered delivery
 
 }  // namespace snn

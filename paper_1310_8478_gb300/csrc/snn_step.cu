@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(1024) k_deliver(DevNet n, const int *t_now)
         for (int e0 = lane; e0 < tile_len; e0 += 32 * kUnroll) {
             int64_t k[kUnroll];
             uint32_t inf[kUnroll], tg[kUnroll];
-            int32_t wk[kUnroll], sk[kUnroll], ls[kUnroll];
+            int32_t wk[kUnroll], ls[kUnroll];
 #pragma unroll
             for (int u = 0; u < kUnroll; ++u) {
                 const int e = e0 + 32 * u;
@@ -144,7 +144,6 @@ __global__ void __launch_bounds__(1024) k_deliver(DevNet n, const int *t_now)
                     }
                     inf[u] = w_info[j];
                     wk[u] = n.w[k[u]];
-                    sk[u] = ((inf[u] & 1u) && stdp) ? n.sd[k[u]] : 0;
                     tg[u] = target_gid(n, inf[u] >> 1, k[u]);
                     if (out_of_range(n, tg[u] < n.N)) k[u] = -1;
                 }
@@ -161,7 +160,7 @@ __global__ void __launch_bounds__(1024) k_deliver(DevNet n, const int *t_now)
                 const int lag = t - ls[u];                     // >= 1
                 if (lag < kLut) {
                     const int32_t a = s_lut[lag];
-                    if (a) n.sd[k[u]] = sk[u] - a;
+                    if (a) red_add(&n.sd[k[u]], -a);
                 }
             }
         }
@@ -180,35 +179,55 @@ __global__ void __launch_bounds__(1024) k_deliver(DevNet n, const int *t_now)
 // sparse S1, column by column (generated nets with compact targets).  A
 // persistent grid takes source columns from a step-wide cursor, so the
 // columns in flight form a narrow band of the torus and so do the targets
-// they reach.  A warp scans 32 rows of the column at a time, turns every
-// delay bucket d whose source fired at t - d into an item, and walks the
-// concatenated synapses of 32 items with all lanes.
+// they reach.  Per column, every thread first issues its share of the loads
+// of the column's spike-history words and its neurons' last spikes (one
+// round of latency for the whole column).  Then the warps take 32-row groups
+// from a block cursor, the inhibitory groups first (an inhibitory spike
+// delivers its whole row at delay 1, an excitatory one a single delay
+// bucket: longest work first, so the warps finish the column together); a
+// warp turns every delay bucket d whose source fired at t - d into an item
+// and walks the 8-synapse chunks of 32 items with all lanes, one 16-byte
+// load of 8 targets (and of 4 weights / derivatives twice) per chunk.
 //   kStage (steps with many events): the input accumulators and LTD amounts
 //   of the 13 columns the block's synapses reach are staged in shared memory,
 //   so an event costs a shared atomic and a shared load; the input is flushed
 //   with one coalesced reduction per touched neuron.
-//   otherwise: an event is an L2 reduction into the target's input and a
-//   gather of its last spike, both on the band of columns in flight, which
-//   stays in L2 (the ring-list order of k_deliver sweeps the whole torus once
-//   per delay instead).
+//   otherwise: only the source column's own neurons are staged (the targets
+//   of every inhibitory synapse and of the local share of the excitatory
+//   ones); an event on another column is an L2 reduction into the target's
+//   input and a gather of its last spike, both on the band of columns in
+//   flight, which stays in L2.
 // ---------------------------------------------------------------------------
 constexpr int kItemCap = 96;                // per warp: pending (row, bucket) items
-constexpr int kTileWords = 32 + 33 + 32 + kItemCap;   // per warp: item starts, length prefix, kinds, pending items
+// per warp: first chunk, chunk-count prefix, first / end synapse, kind of each
+// item, pending items
+constexpr int kTileWords = 32 + 33 + 32 + 32 + 32 + kItemCap;
 
 size_t staged_smem_bytes(uint32_t npc, uint32_t block)
 {
-    return (size_t)kLut * 4 + (size_t)kSlots * npc * 4 + (size_t)(block / 32) * kTileWords * 4 +
+    return (size_t)kLut * 4 + (size_t)kSlots * npc * 4 + (size_t)npc * 4 + (size_t)(block / 32) * kTileWords * 4 +
            (((size_t)kSlots * npc * 2 + 15) & ~size_t(15));
 }
 
+size_t ordered_smem_bytes(uint32_t npc, uint32_t block)
+{
+    return (size_t)kLut * 4 + (size_t)npc * 12 + (size_t)(block / 32) * kTileWords * 4;
+}
+
+// s_amt: kStage -> uint16 LTD amounts of the 13 staged columns;
+//        otherwise int32 LTD amounts of the source column's own neurons.
+// s_hist: the history words (bit k: fired at t - k) of the column's rows.
 template <bool kStage>
 __device__ __forceinline__ void deliver_cols(const DevNet &n, int t, int32_t *s_lut, int32_t *s_in, int32_t *s_tile,
-                                             uint16_t *s_x)
+                                             void *s_amt, uint32_t *s_hist)
 {
     __shared__ uint32_t s_col[kSlots];
     __shared__ uint32_t s_unit;
+    __shared__ uint32_t s_grp;                 // row groups of the current column handed out
+    uint16_t *s_x = reinterpret_cast<uint16_t *>(s_amt);
+    int32_t *s_ltd = reinterpret_cast<int32_t *>(s_amt);
     const uint32_t npc = n.npc;
-    const uint32_t nwarps = blockDim.x >> 5;
+    const uint32_t ngroups = (npc + 31) / 32;
     const bool stdp = !(n.flags & SNN_STDP_OFF);
     const bool deliver_on = !(n.flags & SNN_DELIVERY_OFF);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -216,17 +235,24 @@ __device__ __forceinline__ void deliver_cols(const DevNet &n, int t, int32_t *s_
     drive(n, t, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
     const int D = (int)n.D;
     const uint32_t dmask_e = (2u << D) - 2u, dmask_i = (2u << n.D_inh) - 2u;
-    int32_t *w_lo = s_tile + warp * kTileWords;                // [32] column-relative first synapse
-    int32_t *w_start = w_lo + 32;                              // [33] prefix of the lengths
-    int32_t *w_exc = w_start + 33;                             // [32] 1: excitatory row
+    int32_t *w_c0 = s_tile + warp * kTileWords;                // [32] first chunk (column-relative)
+    int32_t *w_start = w_c0 + 32;                              // [33] prefix of the chunk counts
+    int32_t *w_a = w_start + 33;                               // [32] first synapse (column-relative)
+    int32_t *w_b = w_a + 32;                                   // [32] end synapse
+    int32_t *w_exc = w_b + 32;                                 // [32] 1: excitatory row
     uint32_t *w_items = reinterpret_cast<uint32_t *>(w_exc + 32);   // [kItemCap] pending items
     unsigned long long ev_all = 0, ev_exc = 0;
     for (uint32_t col = blockIdx.x; col < n.C;) {
         if (threadIdx.x < kSlots) s_col[threadIdx.x] = (uint32_t)n.nbr[col * kSlotStride + threadIdx.x];
-        __syncthreads();
+        if (threadIdx.x == 0) s_grp = 0;
+        if (kStage) __syncthreads();
+        // one round of loads for the whole column: history words, and the
+        // staged neurons' last spikes turned into LTD amounts at lag
+        // t - last_spike >= 1 (saturated at the table end, whose entry is 0)
+        for (uint32_t loc = threadIdx.x; loc < npc; loc += blockDim.x)
+            s_hist[loc] = deliver_on ? n.hl[col * npc + loc].x : 0u;
         if (kStage) {
-            // the LTD amount (at most 15 bits: the host checks the table) of every
-            // staged neuron at its lag t - last_spike >= 1, saturated at the table end
+            // at most 15 bits per amount: the host checks the table
             for (int sl = 0; sl < kSlots; ++sl) {
                 const int32_t *ls = n.last_spike + (size_t)s_col[sl] * npc;
                 uint16_t *x_row = s_x + sl * npc;
@@ -236,93 +262,107 @@ __device__ __forceinline__ void deliver_cols(const DevNet &n, int t, int32_t *s_
                     in_row[loc] = 0;
                 }
             }
-            __syncthreads();
+        } else {
+            const int32_t *ls = n.last_spike + (size_t)col * npc;
+            for (uint32_t loc = threadIdx.x; loc < npc; loc += blockDim.x) {
+                s_ltd[loc] = stdp ? s_lut[min(t - ls[loc], kLut - 1)] : 0;
+                s_in[loc] = 0;
+            }
         }
-        const int64_t cbase = (int64_t)col * npc * n.uniform_m;   // first synapse of the column
+        __syncthreads();
+        const int64_t cbase = (int64_t)col * npc * n.uniform_m;   // first synapse of the column (8-aligned)
+        const uint4 *t4 = reinterpret_cast<const uint4 *>(n.tgt16 + cbase);
+        const int4 *w4 = reinterpret_cast<const int4 *>(n.w + cbase);
+        const int64_t col_syn = (int64_t)npc * n.uniform_m;       // synapse slots of the column
         // one tile: lane i takes item (row r, bucket d) when valid, the warp
-        // prefix-sums the bucket lengths and walks the concatenated synapses
+        // prefix-sums the items' chunk counts and walks the concatenated
+        // chunks with all lanes
         auto tile = [&](uint32_t r, int d, bool valid) {
-            int len = 0, lo = 0, exc = 0;
+            int a = 0, b = 0, exc = 0, c0 = 0, nch = 0;
             if (valid) {
                 const uint16_t *off = n.doff + (size_t)(col * npc + r) * kDoffStride;
-                const int a = off[d - 1];
-                len = (int)off[d] - a;
-                lo = (int)(r * n.uniform_m) + a;
+                a = (int)(r * n.uniform_m) + off[d - 1];
+                b = (int)(r * n.uniform_m) + off[d];
                 exc = r < n.ne ? 1 : 0;
+                c0 = a >> 3;
+                nch = b > a ? ((b - 1) >> 3) - c0 + 1 : 0;
             }
-            int incl = len;
+            int incl = nch;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 const int y = __shfl_up_sync(0xffffffffu, incl, o);
                 if (lane >= o) incl += y;
             }
-            const int tile_len = __shfl_sync(0xffffffffu, incl, 31);
-            const int exc_len = __reduce_add_sync(0xffffffffu, exc ? len : 0);
-            w_lo[lane] = lo;
-            w_start[lane] = incl - len;
+            const int total = __shfl_sync(0xffffffffu, incl, 31);
+            const int len_all = __reduce_add_sync(0xffffffffu, b - a);
+            const int len_exc = __reduce_add_sync(0xffffffffu, exc ? b - a : 0);
+            w_c0[lane] = c0;
+            w_start[lane] = incl - nch;
+            w_a[lane] = a;
+            w_b[lane] = b;
             w_exc[lane] = exc;
             if (lane == 0) {
-                w_start[32] = tile_len;
-                ev_all += (unsigned long long)tile_len;
-                ev_exc += (unsigned long long)exc_len;
+                w_start[32] = total;
+                ev_all += (unsigned long long)len_all;
+                ev_exc += (unsigned long long)len_exc;
             }
             __syncwarp();
-            // kUnroll synapses per lane in flight: targets, weights and
-            // derivatives first, then the updates
             int j = 0;
-            for (int e0 = lane; e0 < tile_len; e0 += 32 * kUnroll) {
-                int64_t k[kUnroll];
-                uint32_t v[kUnroll];
-                int32_t wk[kUnroll], sk[kUnroll], ls[kUnroll];
-                bool ex[kUnroll];
+            for (int e = lane; e < total; e += 32) {
+                while (w_start[j + 1] <= e) ++j;
+                const int c = w_c0[j] + (e - w_start[j]);
+                const int k0 = 8 * c;                               // column-relative first synapse
+                const int ia = w_a[j], ib = w_b[j];
+                const bool ex = w_exc[j] != 0;
+                if (out_of_range(n, k0 >= 0 && k0 + 8 <= col_syn && cbase + k0 + 8 <= n.S)) continue;
+                // positions of the chunk inside the item's bucket
+                const uint32_t lo_u = (uint32_t)max(ia - k0, 0), hi_u = (uint32_t)min(ib - k0, 8);
+                const uint32_t mask = ((1u << hi_u) - 1u) & ~((1u << lo_u) - 1u);
+                const uint4 tv = t4[c];
+                int4 wa = make_int4(n.w_inh, n.w_inh, n.w_inh, n.w_inh), wb = wa;
+                if (ex) {
+                    wa = w4[2 * c];
+                    wb = w4[2 * c + 1];
+                }
+                const uint32_t tw[4] = {tv.x, tv.y, tv.z, tv.w};
+                const int32_t wk[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+                int32_t am[8];                                      // LTD amount, or (remote) last spike
+                uint32_t remote = 0;                                // bit u: target on another column
 #pragma unroll
-                for (int u = 0; u < kUnroll; ++u) {
-                    const int e = e0 + 32 * u;
-                    k[u] = -1;
-                    if (e < tile_len) {
-                        while (w_start[j + 1] <= e) ++j;
-                        k[u] = cbase + w_lo[j] + (e - w_start[j]);
-                        if (out_of_range(n, k[u] < n.S)) {
-                            k[u] = -1;
-                            continue;
+                for (int u = 0; u < 8; ++u) {
+                    am[u] = 0;
+                    if (!((mask >> u) & 1u)) continue;
+                    const uint32_t v = (tw[u >> 1] >> (16 * (u & 1))) & 0xffffu;
+                    if (out_of_range(n, v < kSlots * npc)) continue;
+                    if (kStage) {
+                        atomicAdd(&s_in[v], wk[u]);
+                        am[u] = (ex && stdp) ? (int32_t)s_x[v] : 0;
+                    } else {
+                        const uint32_t slot = __umulhi(v, n.npc_recip);
+                        const uint32_t loc = v - slot * npc;
+                        if (slot == 0) {
+                            atomicAdd(&s_in[loc], wk[u]);
+                            am[u] = (ex && stdp) ? s_ltd[loc] : 0;
+                        } else {
+                            const uint32_t g = s_col[slot] * npc + loc;          // target gid
+                            red_add(&n.I[g], wk[u]);
+                            if (ex && stdp) {
+                                am[u] = n.last_spike[g];
+                                remote |= 1u << u;
+                            }
                         }
-                        ex[u] = w_exc[j] != 0;
-                        v[u] = n.tgt16[k[u]];
-                        if (out_of_range(n, v[u] < kSlots * npc)) {
-                            k[u] = -1;
-                            continue;
-                        }
-                        wk[u] = ex[u] ? n.w[k[u]] : n.w_inh;
-                        sk[u] = (ex[u] && stdp) ? n.sd[k[u]] : 0;
                     }
                 }
-                if (kStage) {
+                if (ex && stdp) {
 #pragma unroll
-                    for (int u = 0; u < kUnroll; ++u) {
-                        if (k[u] < 0) continue;
-                        atomicAdd(&s_in[v[u]], wk[u]);
-                        if (ex[u] && stdp) {
-                            const int32_t a = s_x[v[u]];
-                            if (a) n.sd[k[u]] = sk[u] - a;
+                    for (int u = 0; u < 8; ++u) {
+                        if (!((mask >> u) & 1u)) continue;
+                        int32_t x = am[u];
+                        if ((remote >> u) & 1u) {
+                            const int lag = t - x;                            // >= 1
+                            x = lag < kLut ? s_lut[lag] : 0;
                         }
-                    }
-                } else {
-#pragma unroll
-                    for (int u = 0; u < kUnroll; ++u) {
-                        if (k[u] < 0) continue;
-                        const uint32_t slot = __umulhi(v[u], n.npc_recip);
-                        v[u] = s_col[slot] * npc + (v[u] - slot * npc);      // target gid
-                        red_add(&n.I[v[u]], wk[u]);
-                        ls[u] = (ex[u] && stdp) ? n.last_spike[v[u]] : 0;
-                    }
-#pragma unroll
-                    for (int u = 0; u < kUnroll; ++u) {
-                        if (k[u] < 0 || !(ex[u] && stdp)) continue;
-                        const int lag = t - ls[u];                         // >= 1
-                        if (lag < kLut) {
-                            const int32_t a = s_lut[lag];
-                            if (a) n.sd[k[u]] = sk[u] - a;
-                        }
+                        if (x) red_add(&n.sd[cbase + k0 + u], -x);     // no load: most amounts are 0
                     }
                 }
             }
@@ -333,7 +373,7 @@ __device__ __forceinline__ void deliver_cols(const DevNet &n, int t, int32_t *s_
         // few rows of a group fired; a group with too many items for the
         // buffer is walked directly, one flagged bucket per lane and pass.
         int cnt = 0;                                   // items in the buffer
-        uint32_t rb = warp * 32;                       // next row group to scan
+        bool groups_left = true;                       // warp-uniform
         uint32_t fb = 0, r = 0;                        // a group walked directly: its remaining flags
         for (;;) {
             uint32_t tr = 0;
@@ -345,18 +385,24 @@ __device__ __forceinline__ void deliver_cols(const DevNet &n, int t, int32_t *s_
                 fb &= fb - 1u;
                 tr = r;
                 tv = td != 0;
-            } else if (cnt >= 32 || (cnt > 0 && rb >= npc)) {
+            } else if (cnt >= 32 || (cnt > 0 && !groups_left)) {
                 const int take = min(cnt, 32);
                 cnt -= take;
                 const uint32_t it = lane < take ? w_items[cnt + lane] : 0u;
                 tr = it >> 5;
                 td = (int)(it & 31u);
                 tv = lane < take;
-            } else if (rb < npc) {
-                r = rb + lane;
-                rb += nwarps * 32;
+            } else if (groups_left) {
+                uint32_t g = 0;
+                if (lane == 0) g = atomicAdd(&s_grp, 1u);
+                g = __shfl_sync(0xffffffffu, g, 0);
+                if (g >= ngroups) {
+                    groups_left = false;
+                    continue;
+                }
+                r = (ngroups - 1u - g) * 32u + lane;   // the last groups (inhibitory rows) first
                 uint32_t f = 0;                        // bit d: the row's source fired at t - d
-                if (r < npc && deliver_on) f = (n.hl[col * npc + r].x << 1) & (r < n.ne ? dmask_e : dmask_i);
+                if (r < npc) f = (s_hist[r] << 1) & (r < n.ne ? dmask_e : dmask_i);
                 const int mine = __popc(f);
                 int incl = mine;
 #pragma unroll
@@ -392,6 +438,12 @@ __device__ __forceinline__ void deliver_cols(const DevNet &n, int t, int32_t *s_
                     if (x) red_add(&dst[loc], x);
                 }
             }
+        } else {
+            int32_t *dst = n.I + (size_t)col * npc;
+            for (uint32_t loc = threadIdx.x; loc < npc; loc += blockDim.x) {
+                const int32_t x = s_in[loc];
+                if (x) red_add(&dst[loc], x);
+            }
         }
         if (threadIdx.x == 0) s_unit = gridDim.x + atomicAdd(&n.ctr->staged_cursor, 1u);
         __syncthreads();
@@ -414,18 +466,24 @@ __global__ void __launch_bounds__(kStagedBlock) k_deliver_cols(DevNet n, const i
     const uint32_t npc = n.npc, nwarps = blockDim.x >> 5;
     int32_t *s_lut = reinterpret_cast<int32_t *>(smem_i4);
     int32_t *s_in = s_lut + kLut;                                        // [kSlots * npc]
-    int32_t *s_tile = s_in + kSlots * npc;                               // [nwarps][kTileWords]
+    uint32_t *s_hist = reinterpret_cast<uint32_t *>(s_in + kSlots * npc);   // [npc]
+    int32_t *s_tile = reinterpret_cast<int32_t *>(s_hist + npc);         // [nwarps][kTileWords]
     uint16_t *s_x = reinterpret_cast<uint16_t *>(s_tile + nwarps * kTileWords);   // [kSlots * npc]
-    deliver_cols<true>(n, t, s_lut, s_in, s_tile, s_x);
+    deliver_cols<true>(n, t, s_lut, s_in, s_tile, s_x, s_hist);
 }
 
-__global__ void __launch_bounds__(kOrderedBlock) k_deliver_ordered(DevNet n, const int *t_now)
+__global__ void __launch_bounds__(1024) k_deliver_ordered(DevNet n, const int *t_now)
 {
-    __shared__ int32_t s_lut[kLut];
-    __shared__ int32_t s_tile[(kOrderedBlock / 32) * kTileWords];
+    extern __shared__ int4 smem_i4[];
     const int t = *t_now;
     if (!ordered_selected(n, t)) return;
-    deliver_cols<false>(n, t, s_lut, nullptr, s_tile, nullptr);
+    const uint32_t npc = n.npc;
+    int32_t *s_lut = reinterpret_cast<int32_t *>(smem_i4);
+    int32_t *s_in = s_lut + kLut;                                        // [npc]
+    int32_t *s_ltd = s_in + npc;                                         // [npc]
+    uint32_t *s_hist = reinterpret_cast<uint32_t *>(s_ltd + npc);        // [npc]
+    int32_t *s_tile = reinterpret_cast<int32_t *>(s_hist + npc);         // [nwarps][kTileWords]
+    deliver_cols<false>(n, t, s_lut, s_in, s_tile, s_ltd, s_hist);
 }
 
 // ---------------------------------------------------------------------------
@@ -433,10 +491,14 @@ __global__ void __launch_bounds__(kOrderedBlock) k_deliver_ordered(DevNet n, con
 // its incoming excitatory synapses.  The nearest arrival with t_pre + d <=
 // t - 1 is the lowest set bit k >= d of the source's 32-step history (lag
 // k - d), else its latest older spike last_old (lag t - 1 - last_old - d).
+// Reverse entries are 4 bytes on nets with compact targets (the source as
+// slot * npc + local id relative to the target's column, the delay and the
+// source row position; see rin32_entry) and 8 bytes otherwise.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024) k_ltp(DevNet n, const int *t_now, int force)
 {
     __shared__ int32_t s_lut[kLut];
+    __shared__ int32_t s_nb[32][kSlotStride];        // per warp: the neighbour columns of its target
     const int t = *t_now;
     const int tp = t - 1;
     if (n.ctr->ltp_pending != tp || (n.flags & SNN_STDP_OFF)) return;
@@ -447,67 +509,98 @@ __global__ void __launch_bounds__(1024) k_ltp(DevNet n, const int *t_now, int fo
     const int ce = n.ring_cnt[2 * slot], ci = n.ring_cnt[2 * slot + 1];
     const int total = ce + ci;
     const int32_t *ring = n.ring_ids + (size_t)slot * n.N;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+    const bool compact = n.rin32 != nullptr;
+    int32_t *nb = s_nb[warp];
     auto spiker = [&](uint32_t item) -> int32_t {
         return (int)item < ce ? ring[item] : ring[n.N - 1 - ((int)item - ce)];
     };
     // the reverse-entry ranges of the warp's next two spikers are known one
     // item ahead, and the next one's entries go to L2 while this one is walked
+    // (compact entries: lanes 0..15 hold the neighbour columns of those
+    // spikers' columns, loaded as far ahead)
     const uint32_t first = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int64_t lo1 = 0, hi1 = 0, lo2 = 0, hi2 = 0;
+    int32_t nb1 = 0, nb2 = 0;
+    auto neighbours = [&](int32_t p) -> int32_t {
+        return (compact && lane < kSlotStride) ? n.nbr[((uint32_t)p / n.npc) * kSlotStride + lane] : 0;
+    };
     if (first < (uint32_t)total) {
         const int32_t p = spiker(first);
         lo1 = n.rin_off[p];
         hi1 = n.rin_off[p + 1];
+        nb1 = neighbours(p);
     }
     if (first + warps < (uint32_t)total) {
         const int32_t p = spiker(first + warps);
         lo2 = n.rin_off[p];
         hi2 = n.rin_off[p + 1];
+        nb2 = neighbours(p);
     }
     for (uint32_t item = first; item < (uint32_t)total; item += warps) {
         const int64_t lo = lo1, hi = hi1;
+        if (compact) {
+            if (lane < kSlotStride) nb[lane] = nb1;
+            __syncwarp();
+        }
         lo1 = lo2;
         hi1 = hi2;
+        nb1 = nb2;
         if (lane == 0 && hi1 > lo1) {
-            prefetch_inside(n.rin + lo1, (size_t)(hi1 - lo1) * 8);
-            prefetch_inside(n.sd_rev + lo1, (size_t)(hi1 - lo1) * 4);
+            if (compact) prefetch_inside(n.rin32 + lo1, (size_t)(hi1 - lo1) * 4);
+            else prefetch_inside(n.rin + lo1, (size_t)(hi1 - lo1) * 8);
         }
         if (item + 2 * warps < (uint32_t)total) {
             const int32_t p = spiker(item + 2 * warps);
             lo2 = n.rin_off[p];
             hi2 = n.rin_off[p + 1];
+            nb2 = neighbours(p);
         }
         // kUnroll entries per lane: reverse entries, then the sources'
-        // histories and the synapses' derivatives (independent) in one round
+        // histories, then a reduction of every non-zero amount into the
+        // entry's accumulator (no load: an entry whose source did not fire
+        // inside the window costs its 4 or 8 bytes and nothing else)
         for (int64_t e0 = lo + lane; e0 < hi; e0 += 32 * kUnroll) {
-            uint64_t r[kUnroll];
+            uint32_t src[kUnroll], dl[kUnroll];
+            bool ok[kUnroll];
 #pragma unroll
             for (int u = 0; u < kUnroll; ++u) {
-                r[u] = (e0 + 32 * u < hi && !out_of_range(n, e0 + 32 * u < n.n_rin)) ? n.rin[e0 + 32 * u] : ~0ull;
-                if (r[u] != ~0ull && out_of_range(n, (uint32_t)r[u] < n.N)) r[u] = ~0ull;
+                const int64_t e = e0 + 32 * u;
+                ok[u] = e < hi && !out_of_range(n, e < n.n_rin);
+                if (!ok[u]) continue;
+                if (compact) {
+                    const uint32_t r = n.rin32[e];
+                    const uint32_t v = r & 0xffffu;
+                    const uint32_t sl = __umulhi(v, n.npc_recip);
+                    src[u] = (uint32_t)nb[sl] * n.npc + (v - sl * n.npc);
+                    dl[u] = (r >> 16) & 31u;
+                } else {
+                    const uint64_t r = n.rin[e];
+                    src[u] = (uint32_t)r;
+                    dl[u] = (uint32_t)(r >> 48);
+                }
+                if (out_of_range(n, src[u] < n.N)) ok[u] = false;
             }
             uint2 h[kUnroll];
-            int32_t sv[kUnroll];
 #pragma unroll
             for (int u = 0; u < kUnroll; ++u) {
-                if (r[u] == ~0ull) continue;
-                h[u] = n.hl[(uint32_t)r[u]];
-                sv[u] = n.sd_rev[e0 + 32 * u];
+                if (!ok[u]) continue;
+                h[u] = n.hl[src[u]];
             }
 #pragma unroll
             for (int u = 0; u < kUnroll; ++u) {
-                if (r[u] == ~0ull) continue;
-                const uint32_t d = (uint32_t)(r[u] >> 48);
+                if (!ok[u]) continue;
+                const uint32_t d = dl[u];
                 const uint32_t recent = h[u].x & (0xffffffffu << d);
                 const int lag = recent ? (__ffs(recent) - 1 - (int)d) : (tp - (int)h[u].y - (int)d);
                 if (lag < kLut) {
                     const int32_t a = s_lut[lag];
-                    if (a) n.sd_rev[e0 + 32 * u] = sv[u] + a;   // coalesced: the target's entries are contiguous
+                    if (a) red_add(&n.sd_rev[e0 + 32 * u], a);   // coalesced: the target's entries are contiguous
                 }
             }
         }
+        __syncwarp();
     }
 }
 
@@ -521,36 +614,61 @@ __global__ void __launch_bounds__(1024) k_fold(DevNet n, const int *t_now, int f
         const int t = *t_now;        // only before a long-term update (t closes a period)
         if (!n.deriv_period || t <= 0 || (t % (int)n.deriv_period) != 0) return;
     }
-    // Chunks of consecutive reverse entries (targets in order) are handed out
-    // in order, so the targets in flight form a narrow band of the torus and
-    // so do the source rows their synapses scatter into: the scatter stays in
-    // L2.  Four entries per thread in flight.
-    __shared__ int64_t s_chunk;
-    constexpr int64_t kChunk = 8192;
-    for (int64_t c0 = (int64_t)blockIdx.x * kChunk; c0 < n.n_rin;) {
-        const int64_t c1 = min(c0 + kChunk, n.n_rin);
-        for (int64_t e0 = c0 + threadIdx.x; e0 < c1; e0 += 4 * (int64_t)blockDim.x) {
-            int32_t v[4];
-            uint64_t r[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int64_t e = e0 + u * (int64_t)blockDim.x;
-                v[u] = e < c1 ? n.sd_rev[e] : 0;
+    // Chunks of kFoldTargets consecutive targets are handed out in order, so
+    // the targets in flight form a narrow band of the torus and so do the
+    // source rows their synapses scatter into: the scatter stays in L2.  A
+    // warp takes one target at a time, four entries per lane in flight.
+    __shared__ uint32_t s_chunk;
+    __shared__ int32_t s_nb[32][kSlotStride];
+    constexpr uint32_t kFoldTargets = 64;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const bool compact = n.rin32 != nullptr;
+    int32_t *nb = s_nb[warp];
+    for (uint32_t c0 = blockIdx.x * kFoldTargets; c0 < n.N;) {
+        const uint32_t c1 = min(c0 + kFoldTargets, n.N);
+        for (uint32_t p = c0 + warp; p < c1; p += nw) {
+            const int64_t lo = n.rin_off[p], hi = n.rin_off[p + 1];
+            if (compact) {
+                if (lane < kSlotStride) nb[lane] = n.nbr[(p / n.npc) * kSlotStride + lane];
+                __syncwarp();
             }
+            for (int64_t e0 = lo + lane; e0 < hi; e0 += 32 * 4) {
+                int32_t v[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
-                if (v[u]) r[u] = n.rin[e0 + u * (int64_t)blockDim.x];
+                for (int u = 0; u < 4; ++u) {
+                    const int64_t e = e0 + 32 * u;
+                    v[u] = (e < hi && !out_of_range(n, e < n.n_rin)) ? n.sd_rev[e] : 0;
+                }
+                int64_t fwd[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                if (!v[u]) continue;
-                const int64_t fwd = row_base(n, (uint32_t)r[u]) + ((uint32_t)(r[u] >> 32) & 0xffffu);
-                if (out_of_range(n, (uint32_t)r[u] < n.N && fwd < n.S)) continue;
-                n.sd[fwd] += v[u];
-                n.sd_rev[e0 + u * (int64_t)blockDim.x] = 0;
+                for (int u = 0; u < 4; ++u) {
+                    if (!v[u]) continue;
+                    uint32_t src, pos;
+                    if (compact) {
+                        const uint32_t r = n.rin32[e0 + 32 * u];
+                        const uint32_t x = r & 0xffffu;
+                        const uint32_t sl = __umulhi(x, n.npc_recip);
+                        src = (uint32_t)nb[sl] * n.npc + (x - sl * n.npc);
+                        pos = r >> 21;
+                    } else {
+                        const uint64_t r = n.rin[e0 + 32 * u];
+                        src = (uint32_t)r;
+                        pos = (uint32_t)(r >> 32) & 0xffffu;
+                    }
+                    fwd[u] = row_base(n, src) + pos;
+                    if (out_of_range(n, src < n.N && fwd[u] < n.S)) v[u] = 0;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (!v[u]) continue;
+                    red_add(&n.sd[fwd[u]], v[u]);
+                    n.sd_rev[e0 + 32 * u] = 0;
+                }
             }
+            __syncwarp();
         }
         __syncthreads();
-        if (threadIdx.x == 0) s_chunk = (int64_t)(gridDim.x + atomicAdd(&n.ctr->fold_cursor, 1u)) * kChunk;
+        if (threadIdx.x == 0) s_chunk = (gridDim.x + atomicAdd(&n.ctr->fold_cursor, 1u)) * kFoldTargets;
         __syncthreads();
         c0 = s_chunk;
     }

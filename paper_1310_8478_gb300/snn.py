@@ -77,6 +77,13 @@ class SnnProfile(ctypes.Structure):
                 ("dense_ltp_visits", ctypes.c_int64), ("kernels", ctypes.c_int64)]
 
 
+class SnnAtomicRates(ctypes.Structure):
+    _fields_ = [("red_global_random_gops", ctypes.c_double), ("red_global_window_gops", ctypes.c_double),
+                ("red_global_coalesced_gops", ctypes.c_double), ("ld_global_random_gops", ctypes.c_double),
+                ("atom_shared_window_gops", ctypes.c_double), ("array_bytes", ctypes.c_double),
+                ("threads", ctypes.c_double)]
+
+
 SPIKE_DTYPE = np.dtype([("t", np.int32), ("gid", np.int32)])
 STIM_DTYPE = np.dtype([("t", np.int32), ("gid", np.int32), ("q16", np.int32)])
 KERNELS = ("deliver", "neuron", "ltp", "deriv", "dense")
@@ -121,6 +128,7 @@ _SIGS = {
     "snn_batch_free": (None, [_vp]),
     "snn_thalamic_events": (ctypes.c_int, [_P(SnnConfig), ctypes.c_int32, ctypes.c_uint32, _vp, ctypes.c_size_t,
                                            _P(ctypes.c_size_t)]),
+    "snn_microbench_atomics": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_uint32, _vp, _P(SnnAtomicRates)]),
     "snn_free": (None, [_vp]),
     "snn_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "snn_last_error": (ctypes.c_char_p, []),
@@ -311,6 +319,15 @@ def snn_thalamic_events(cfg: dict, t0: int, n_ms: int) -> np.ndarray:
 # ---------------------------------------------------------------------------
 # convenience wrapper
 # ---------------------------------------------------------------------------
+def snn_microbench_atomics(array_bytes: int, ops_per_thread: int = 4096, stream=None) -> dict:
+    """Rates (1e9 operations / s) of scattered L2 reductions, gathers and
+    shared-memory atomics on this GPU (see include/snn.h)."""
+    r = SnnAtomicRates()
+    _check(load().snn_microbench_atomics(int(array_bytes), int(ops_per_thread), _stream_handle(stream),
+                                         ctypes.byref(r)), "snn_microbench_atomics")
+    return {name: getattr(r, name) for name, _ in SnnAtomicRates._fields_}
+
+
 class Network:
     """One network on the device.  cfg: a parameter dictionary (workloads.py)."""
 

@@ -69,9 +69,10 @@ def _args(**kw):
     return types.SimpleNamespace(**a)
 
 
-def _fake_sample(seconds, warmup_steps=0, max_steps=None):
+def _fake_sample(seconds, t0, t1):
+    # the oracle is timed over the GPU leg's window of steps
     return dict(value=1.5e7, unit="events/s", cores=1, kind="oracle", sample="fake sample",
-                steps=max_steps, seconds=0.5, events=7.5e6)
+                steps=t1 - t0, seconds=0.5, events=7.5e6)
 
 
 def test_reference_arm_prints_one_complete_line(monkeypatch):
@@ -192,6 +193,11 @@ class _FakeBenchNet:
     def raster_reset(self):
         pass
 
+    def raster(self, t0=0, t1=None):
+        import numpy as np
+        t = np.arange(t0, t1, dtype=np.int32)
+        return t, (t * 7) % self.n
+
     def get_launch(self):
         return {"graph_steps": 50}
 
@@ -233,7 +239,10 @@ def test_main_line_carries_every_key_with_a_fake_engine(monkeypatch, capsys):
     monkeypatch.setattr(serve, "snn", types.SimpleNamespace(Network=ts.FakeNet, Batch=ts.FakeBatch,
                                                             SnnError=ts.FakeError, ENOMEM=ts.ENOMEM))
     ts.FakeNet.live.clear()
-    monkeypatch.setattr(bench, "oracle_sample", lambda seconds: _fake_sample(seconds, max_steps=7))
+    monkeypatch.setattr(bench, "oracle_sample", lambda seconds, t0, t1: _fake_sample(seconds, t0, t1))
+    monkeypatch.setattr(pkg.snn, "snn_microbench_atomics",
+                        lambda nbytes, ops, stream=None: {"red_global_window_gops": 200.0,
+                                                          "atom_shared_window_gops": 2000.0})
     monkeypatch.setattr(bench, "dist_env", lambda: (0, 0, 1))
     monkeypatch.setattr(sys, "argv", ["bench.py", "--steps", "5", "--warmup", "3", "--serve-requests", "4"])
     assert bench.main() == 0
@@ -257,3 +266,11 @@ def test_main_line_carries_every_key_with_a_fake_engine(monkeypatch, capsys):
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
     assert line["serve"]["requests"] == 4 and "p99_s" in line["serve"]["latency"]
     assert line["kernels"]["deriv"]["alg_gbs"] == 0.0                # no period closes in steps 3..7
+    # the oracle is timed over the GPU leg's steps; the end-to-end leg
+    # compares its raster with the device run's
+    assert line["e2e"]["raster_sha256_equals_device_run"] is True
+    assert line["roofline"]["atomic"]["red_global_window_per_s"] == 200e9
+    st = line["steady"]
+    assert st["dense_regime"]["steps"] == [60, 70] and st["period_end"]["steps"] == [995, 1005]
+    assert st["dense_regime"]["dense_fused"]["bytes_per_step"] == pytest.approx(
+        2.0 * 64 * 64 * 1250 * 1125 + 12.0 * 64 * 64 * 1000 * 1125)
