@@ -51,6 +51,10 @@ def parse_args():
     ap.add_argument("--batch-bench", type=int, default=0, metavar="NETS",
                     help="instead: the uneven batched workload (first NETS of 256 nets), batched vs one at a time")
     ap.add_argument("--batch-budget-gb", type=float, default=150.0, help="device budget of one wave of nets")
+    ap.add_argument("--batch-steps", type=int, default=100, help="steps of each net in the batch leg")
+    ap.add_argument("--batch-nets", type=int, default=256, help="nets of the batch leg of the default line (0: none)")
+    ap.add_argument("--batch-autotune-ms", type=int, default=0,
+                    help="probe steps of the batch autotuner before the timed batch (0: default shape)")
     ap.add_argument("--serve-bench", type=int, default=0, metavar="REQUESTS",
                     help="instead: the serving workload (Poisson arrivals) with this many requests")
     ap.add_argument("--serve-rate", type=float, default=200.0, help="mean arrivals per second")
@@ -140,20 +144,37 @@ class ClockSampler:
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, period_ms: int = 20):
         self.path = tempfile.mktemp(prefix="clocks_", suffix=".csv")
         self.proc = None
         try:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + self.FIELDS,
-                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+                 "--format=csv,noheader,nounits", "-lms", str(period_ms)], stdout=self.f, stderr=subprocess.DEVNULL)
+            # the first sample is taken before the timed region starts
+            self._wait_lines(1, 5.0)
         except Exception:
             self.proc = None
+
+    def _lines(self) -> int:
+        try:
+            with open(self.path) as f:
+                return sum(1 for _ in f)
+        except OSError:
+            return 0
+
+    def _wait_lines(self, n: int, timeout_s: float):
+        t0 = time.perf_counter()
+        while self._lines() < n and time.perf_counter() - t0 < timeout_s and self.proc.poll() is None:
+            time.sleep(0.005)
 
     def stop(self):
         if self.proc is None:
             return None
+        # a sample after the timed region too, so that a short region is
+        # bracketed by samples on both sides
+        self._wait_lines(self._lines() + 1, 2.0)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -242,63 +263,99 @@ def measured_peaks():
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
-def run_batch_bench(args):
+def batch_leg(n_nets: int, steps: int, budget_gb: float, stream, autotune_ms: int = 0, warm: int = 10):
     """Independent uneven networks (grid side 1..16, M in {100, 400, 1125},
-    seeds 1000..): every wave of nets that fits the budget advances --steps
-    steps twice from the initial state, once one net after another (each with
-    its own CUDA graphs) and once as one batch (one graph per chunk, nets on
-    parallel branches); throughput = synaptic events / device time."""
+    seeds 1000..): every wave of nets that fits the budget runs twice from
+    the initial state, once one net after another (each with its own CUDA
+    graphs) and once as one batch (one graph per chunk, one launch per kind
+    of kernel per step for all nets): `warm` untimed steps (graph capture),
+    then `steps` timed steps; throughput = synaptic events of the timed steps
+    / their time (CUDA events around the whole wave, host launch overhead
+    included).  Each net's raster digest must be the same both ways."""
+    import torch
+    import paper_1310_8478_gb300 as eng
+    cfgs = workloads.batch_workloads()[:n_nets]
+    budget = int(budget_gb * 1e9)
+    T = warm + steps
+    seq_ms = bat_ms = 0.0
+    seq_ev = bat_ev = 0
+    waves = 0
+    same = True
+    shape = None
+    ev_a = torch.cuda.Event(enable_timing=True)
+    ev_b = torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        ev_a.record(stream)
+        fn()
+        ev_b.record(stream)
+        torch.cuda.synchronize()
+        return ev_a.elapsed_time(ev_b)
+
+    i = 0
+    while i < len(cfgs):
+        wave, used = [], 0
+        while i < len(cfgs):
+            n = eng.Network(cfgs[i], stream=stream, raster_capacity=workloads.n_neurons(cfgs[i]) * T + 1024)
+            if wave and used + n.device_bytes > budget:
+                n.close()
+                break
+            wave.append(n)
+            used += n.device_bytes
+            i += 1
+        waves += 1
+        # one at a time
+        for n in wave:
+            n.run(warm)
+        e0 = sum(n.counters()["e_all"] for n in wave)
+
+        def alone():
+            for n in wave:
+                n.run(steps)
+        seq_ms += timed(alone)
+        seq_ev += sum(n.counters()["e_all"] for n in wave) - e0
+        ref = [raster_digest(n, 0, T) for n in wave]
+        for n in wave:
+            n.reset()
+        # batched
+        with eng.Batch(wave, graph_steps=10) as b:
+            if autotune_ms and shape is None:
+                shape = b.autotune(autotune_ms)
+            elif shape is not None:
+                b.set_launch(**{k: shape[k] for k in ("deliver_block", "deliver_blocks_per_sm",
+                                                      "ltp_blocks_per_sm", "graph_steps")})
+            b.run(warm)
+            e0 = sum(n.counters()["e_all"] for n in wave)
+            bat_ms += timed(lambda: b.run(steps))
+        bat_ev += sum(n.counters()["e_all"] for n in wave) - e0
+        same = same and all(raster_digest(n, 0, T) == d for n, d in zip(wave, ref))
+        for n in wave:
+            n.close()
+    out = {"workload": "%d independent nets, grid side uniform 1..16, M in {100, 400, 1125}, seeds 1000..%d, "
+                       "steps %d..%d of each (after %d untimed), waves under %.0f GB" % (
+                           len(cfgs), 999 + len(cfgs), warm, T - 1, warm, budget_gb),
+           "nets": len(cfgs), "waves": waves, "steps": steps, "unit": "events/s",
+           "value": bat_ev / (bat_ms / 1e3), "batched_ms": round(bat_ms, 3),
+           "one_at_a_time": seq_ev / (seq_ms / 1e3), "one_at_a_time_ms": round(seq_ms, 3),
+           "speedup": (bat_ev / bat_ms) / (seq_ev / seq_ms), "same_events": seq_ev == bat_ev,
+           "raster_digests_equal": same, "events": bat_ev}
+    if shape is not None:
+        out["autotuned"] = {k: shape[k] for k in ("deliver_block", "deliver_blocks_per_sm", "graph_steps")}
+    return out
+
+
+def run_batch_bench(args):
+    """The batched workload alone (see batch_leg), --batch-bench nets."""
     import torch
     import paper_1310_8478_gb300 as eng
     torch.cuda.set_device(0)
     eng.build_engine()
-    cfgs = workloads.batch_workloads()[: args.batch_bench]
-    T = args.steps
-    budget = int(args.batch_budget_gb * 1e9)
     stream = torch.cuda.Stream()
-    seq_s = bat_s = 0.0
-    seq_ev = bat_ev = 0
-    waves = 0
-    i = 0
     with torch.cuda.stream(stream):
-        while i < len(cfgs):
-            wave, used = [], 0
-            while i < len(cfgs):
-                n = eng.Network(cfgs[i], stream=stream, raster_capacity=0)
-                if wave and used + n.device_bytes > budget:
-                    n.close()
-                    break
-                wave.append(n)
-                used += n.device_bytes
-                i += 1
-            waves += 1
-            # one at a time
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            for n in wave:
-                n.run(T)
-            torch.cuda.synchronize()
-            seq_s += time.perf_counter() - t0
-            seq_ev += sum(n.counters()["e_all"] for n in wave)
-            for n in wave:
-                n.reset()
-            # batched
-            with eng.Batch(wave, graph_steps=10) as b:
-                torch.cuda.synchronize()
-                t0 = time.perf_counter()
-                b.run(T)
-                torch.cuda.synchronize()
-                bat_s += time.perf_counter() - t0
-            bat_ev += sum(n.counters()["e_all"] for n in wave)
-            for n in wave:
-                n.close()
-    line = {"metric": "synaptic events/s", "mode": "batch", "unit": "events/s", "n_gpus": 1,
-            "nets": len(cfgs), "waves": waves, "steps": T, "raster": "off",
-            "config": {"workload": "%d independent nets, grid side uniform 1..16, M in {100, 400, 1125}, "
-                                   "seeds 1000.., wave budget %.0f GB" % (len(cfgs), args.batch_budget_gb)},
-            "value": bat_ev / bat_s, "batched_s": bat_s, "one_at_a_time": seq_ev / seq_s,
-            "one_at_a_time_s": seq_s, "speedup": (bat_ev / bat_s) / (seq_ev / seq_s),
-            "same_events": seq_ev == bat_ev, "events": bat_ev}
+        leg = batch_leg(args.batch_bench, args.batch_steps, args.batch_budget_gb, stream, args.batch_autotune_ms)
+    line = {"metric": "synaptic events/s", "mode": "batch", "n_gpus": 1, "config": {"workload": leg["workload"]}}
+    line.update(leg)
     print(json.dumps(line), flush=True)
     return 0
 
@@ -307,7 +364,7 @@ SERVE_WORKLOAD = ("Poisson requests, grid side log-uniform 1..32, M in {100, 400
                   "duration uniform 100..5000 ms, seeds 5000..")
 
 
-def serve_leg(n_requests: int, rate: float, budget_gb: float, stream):
+def serve_leg(n_requests: int, rate: float, budget_gb: float, stream, one_at_a_time: bool = True):
     """Simulation requests arriving as a Poisson stream (mean `rate` per
     second; grid side log-uniform 1..32, M in {100, 400, 1125}, duration
     uniform 100..5000 ms, seeds 5000..) served with continuous batching under
@@ -326,10 +383,26 @@ def serve_leg(n_requests: int, rate: float, budget_gb: float, stream):
     res = srv.serve(reqs)
     wall = time.perf_counter() - t0
     ev = sum(r.events for r in res)
-    return {"requests": len(res), "rate_per_s": rate, "budget_gb": budget_gb,
-            "value": ev / wall, "unit": "events/s", "wall_s": wall, "events": ev,
-            "latency": serve.latency_stats(res), "chunks": srv.chunks, "rebatches": srv.rebatches,
-            "sim_ms_total": int(sum(r.steps for r in res))}
+    out = {"requests": len(res), "rate_per_s": rate, "budget_gb": budget_gb,
+           "value": ev / wall, "unit": "events/s", "wall_s": wall, "events": ev,
+           "latency": serve.latency_stats(res), "chunks": srv.chunks, "rebatches": srv.rebatches,
+           "sim_ms_total": int(sum(r.steps for r in res))}
+    if one_at_a_time:
+        # the same requests, each run alone to completion one after another
+        # (no waiting for arrivals), wall time around the whole sequence
+        ev1 = 0
+        t0 = time.perf_counter()
+        for r in reqs:
+            n = serve.snn.Network(r.cfg, stream=stream, hbm_budget_bytes=int(budget_gb * 1e9), raster_capacity=0)
+            try:
+                n.run(r.duration_ms)
+                ev1 += n.counters()["e_all"]
+            finally:
+                n.close()
+        wall1 = time.perf_counter() - t0
+        out["one_at_a_time"] = {"value": ev1 / wall1, "wall_s": wall1, "same_events": ev1 == ev}
+        out["speedup"] = (ev / wall) / (ev1 / wall1)
+    return out
 
 
 def run_serve_bench(args):
@@ -490,6 +563,15 @@ def main():
                          "us_per_step": round(1000.0 * a0.elapsed_time(a1) / 1000.0, 2),
                          "graph_steps": sn.get_launch()["graph_steps"]}
 
+        # batching: the 256 uneven nets, batched against one at a time
+        batched = None
+        if args.batch_nets > 0 and rank == 0:
+            try:
+                batched = batch_leg(args.batch_nets, args.batch_steps, args.batch_budget_gb, stream,
+                                    args.batch_autotune_ms)
+            except Exception as e:  # noqa: BLE001
+                batched = {"error": "%s: %s" % (type(e).__name__, e)}
+
         # serving: p50 / p99 latency and throughput of a Poisson request
         # stream under continuous batching, after the main net is released;
         # a failure here is reported in the line instead of losing it
@@ -569,6 +651,7 @@ def main():
         "steady": steady,
         "atomics": atomics,
         "small_net": small,
+        "batch": batched,
         "serve": served,
         "cpu_baseline": None if cpu is None else {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")},
         "clocks": clk,

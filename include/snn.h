@@ -116,7 +116,8 @@ typedef struct {
  */
 typedef struct {
     uint32_t deliver_block;          /* threads per block of the event-driven delivery (multiple of 32;
-                                        the column-ordered delivery gives one column to each block) */
+                                        the column-ordered delivery gives one column to each block
+                                        and takes at most 256 threads) */
     uint32_t deliver_blocks_per_sm;  /* resident blocks per SM of the event-driven delivery (at most) */
     uint32_t neuron_block;           /* threads per block of the neuron update */
     uint32_t ltp_block;              /* threads per block of the event-driven potentiation */
@@ -201,6 +202,38 @@ int snn_set_stimulus(snn_net *net, const snn_stimulus *host_events, size_t n);
  */
 int snn_set_thalamic(snn_net *net, int on);
 
+/*
+ * snn_set_tile -- make the net one tile of a torus partitioned by columns,
+ * as the paper's processes own sets of columns (Sec. 2 "Delivery of spiking
+ * messages": a process integrates its own neurons and receives, every step,
+ * the spikes of the other processes' neurons that reach its synapses).  From
+ * the first step on the net integrates only the neurons of columns
+ * [first_col, first_col + n_cols), delivers spikes only to them (from every
+ * source whose synapses reach them, wherever it sits), potentiates only their
+ * incoming synapses, and counts only those events and their spikes; so each
+ * synapse is served by the tile that owns its target.  The spikes of the other
+ * columns' neurons must be supplied after every step with snn_inject_spikes.
+ * The tile keeps the whole torus's state arrays (one GPU holds every tile
+ * here); only ownership is partitioned.  Tiles take the column-ordered
+ * delivery in every step (the dense pass and the staged delivery are off).
+ * first_col = 0, n_cols = all columns makes the net whole again.
+ * Errors: SNN_EINVAL (range outside the torus), SNN_ESTATE (the net has
+ * stepped already, or is not a generated net with compact targets).
+ */
+int snn_set_tile(snn_net *net, uint32_t first_col, uint32_t n_cols);
+
+/*
+ * snn_inject_spikes -- the spikes of the step just completed (t = steps
+ * simulated - 1) of neurons the tile does not own (host array of n gids, any
+ * order, each at most once), as received from their owners: they join the
+ * step's spike lists after the tile's own, and the neurons' spike history and
+ * last spike, so that delivery and potentiation treat them as the tile's own.
+ * Returns after the device has taken them.  Errors: SNN_EINVAL (a gid out of
+ * range, owned by the tile, or repeated), SNN_ESTATE (not a tile, no step
+ * run yet).
+ */
+int snn_inject_spikes(snn_net *net, const int32_t *host_gids, uint32_t n);
+
 /* snn_set_launch / snn_get_launch -- launch shape (see snn_launch). */
 int snn_set_launch(snn_net *net, const snn_launch *launch);
 int snn_get_launch(const snn_net *net, snn_launch *launch);
@@ -262,14 +295,18 @@ int snn_read_synapses(snn_net *net, uint32_t first, uint32_t count, int32_t *hos
  * networks' steps are in flight on other streams, or hosts whose device
  * memory belongs to a framework allocator they cannot reach from here.
  * The device staging is a fixed array compiled into the library
- * (SNN_NOALLOC_MAX_SYNAPSES synapses, about 13 MiB, held by every GPU that
- * loads the library until the process exits).  A range with more synapses
- * is rejected with SNN_EINVAL; split it.  The first call on a device looks
- * up the array's device address with that device current, so make it before
- * any stream capture.  Every call shares the array: calls that overlap on
- * the GPU (different threads, different nets on the same device) race, so
- * serialize them.  Arguments, results and errors otherwise as
- * snn_read_synapses.
+ * (SNN_NOALLOC_MAX_SYNAPSES synapses, about 13 MiB).  It becomes resident on
+ * a device when the first net is built there (the build looks up the array's
+ * device address with that device current, which loads the library's module)
+ * and stays until the process exits; it is not counted in hbm_budget_bytes.
+ * Every build looks the address up again, so a device reset between nets
+ * leaves no stale address; a net that outlives a reset of its device is
+ * invalid anyway.  This call itself does no lookup, so it may come after a
+ * stream capture has started on another stream.  A range with more synapses
+ * is rejected with SNN_EINVAL; split it.  Every call shares the array: calls
+ * that overlap on the GPU (different threads, different nets on the same
+ * device) race, so serialize them.  Arguments, results and errors otherwise
+ * as snn_read_synapses.
  */
 #define SNN_NOALLOC_MAX_SYNAPSES (1u << 20)
 int snn_read_synapses_noalloc(snn_net *net, uint32_t first, uint32_t count, int32_t *host_tgt,
@@ -337,8 +374,12 @@ int snn_autotune(snn_net *net, uint32_t probe_ms, snn_launch *best);
  * Batches: many independent networks on one GPU (the paper's networks of
  * different sizes and fan-outs, Table 3, run side by side).  A batch advances
  * every net it holds with one CUDA-graph launch per chunk of graph_steps
- * steps; each net's kernels form a parallel branch of the graph, so small,
- * launch-bound nets run concurrently instead of one after another.  Each net
+ * steps; inside the chunk every step is one launch per kind of step kernel
+ * for all nets together (each block works for one net, on that net's own
+ * step, counters and cursors; nets get blocks in proportion to their
+ * synapses), so small, launch-bound nets share the GPU with large ones
+ * instead of queueing one after another.  Steps that do not fill a chunk run
+ * each net's own launches on parallel streams.  Each net
  * keeps its own state and step count (nets may stand at different steps and
  * have different periods), bit-identical to running it alone.  The batch
  * owns no net: free the batch before its nets.  All nets must be on the
@@ -357,6 +398,29 @@ int snn_batch_run(snn_batch *batch, uint32_t n_ms);
 
 /* snn_batch_free -- release the batch (not its nets; NULL is allowed). */
 void snn_batch_free(snn_batch *batch);
+
+/*
+ * snn_batch_set_launch / snn_batch_get_launch -- launch shape of the batch's
+ * kernels (deliver_block: threads per column of the column-ordered
+ * delivery; deliver_blocks_per_sm, ltp_blocks_per_sm: resident blocks per SM
+ * of the event-driven kernels, shared out among the nets in proportion to
+ * their synapses; ltp_block, neuron_block, deriv_block, dense_block;
+ * graph_steps: steps per captured chunk, even, >= 2).  Zero fields keep the
+ * current value; the other fields and the nets' own shapes are not used.
+ * Results never depend on the shape.  Errors: SNN_EINVAL.
+ */
+int snn_batch_set_launch(snn_batch *batch, const snn_launch *launch);
+int snn_batch_get_launch(const snn_batch *batch, snn_launch *launch);
+
+/*
+ * snn_batch_autotune -- the batch's own autotuner: every candidate shape
+ * (threads per column of the column-ordered delivery 128 / 256,
+ * resident blocks per SM 4 / 8, steps per chunk 10 / 50) advances every net
+ * probe_ms steps from a reset, timed with CUDA events on the batch's stream;
+ * the fastest shape is kept and every net is left reset at t = 0.  Generated
+ * nets only (SNN_ESTATE otherwise).  *best (may be NULL) receives the shape.
+ */
+int snn_batch_autotune(snn_batch *batch, uint32_t probe_ms, snn_launch *best);
 
 /*
  * snn_reset -- return a generated net to its initial state (t = 0, initial

@@ -62,6 +62,26 @@ constexpr int kMaxDevices = 64;
 int32_t *g_noalloc_ptr[kMaxDevices] = {nullptr};
 std::mutex g_noalloc_mutex;
 
+// device address of the staging array on the current device, looked up
+// again at every net's set-up (so that the module holding the array is
+// loaded before the net's budget is spent, and a device reset between nets
+// leaves no stale address) and kept per device
+int noalloc_lookup(int device, int32_t **out)
+{
+    if (device < 0 || device >= kMaxDevices) { set_error("device ordinal too large"); return SNN_EINVAL; }
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    void *ptr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("cudaGetSymbolAddress of the staging array failed: %s", cudaGetErrorString(e));
+        return SNN_ECUDA;
+    }
+    g_noalloc_ptr[device] = (int32_t *)ptr;
+    *out = (int32_t *)ptr;
+    return SNN_OK;
+}
+
 __global__ void k_fill_row_off(int64_t *row_off, uint32_t n, uint32_t m)
 {
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += gridDim.x * blockDim.x)
@@ -109,6 +129,8 @@ struct snn_net {
     uint16_t *tgt16 = nullptr;
     int32_t *nbr = nullptr;
     bool ltp_owed = false;          // the last step's LTP has not been applied yet
+    int32_t *noalloc_base = nullptr; // device address of the no-allocation staging array
+    int32_t *inject_buf = nullptr;  // tiles: device copy of the spikes received for a step
     bool dense_ok = false;          // the dense pass can run on this net
     int dense_grid = 0;             // blocks of the dense pass (at most one wave of resident blocks)
     int staged_grid = 0;            // blocks of the column-staged delivery (likewise)
@@ -132,16 +154,32 @@ struct snn_net {
     int64_t prof_kernels = 0;       // kernels launched by the profiled steps
 };
 
+// kinds of step kernel a batch launches once per step for all of its nets
+enum BatchKind { kBLtp, kBFold, kBDeriv, kBOrdered, kBRing, kBStaged, kBDense, kBNeuron32, kBNeuron64, kBProbe,
+                 kBKinds };
+
 struct snn_batch {
     std::vector<snn_net *> nets;
     cudaStream_t main = nullptr;
-    std::vector<cudaStream_t> branch;
+    std::vector<cudaStream_t> branch;    // single eager steps: one stream per net
     cudaEvent_t fork = nullptr;
     std::vector<cudaEvent_t> join;
     uint32_t L = 0;
     cudaGraphExec_t graph = nullptr;
     std::vector<uint64_t> versions;      // the nets' versions when the graph was captured
     std::vector<int> parity;             // the nets' step parity when the graph was captured
+    snn_launch launch{};                 // block sizes and resident blocks of the batched kernels
+    int sm_count = 0;
+    int device = 0;
+    // device tables of the batched launches (DevNet copies, parities, and per
+    // kind the first block of every net and the net of every block)
+    void *tables = nullptr;
+    size_t tables_bytes = 0;
+    struct Kind {
+        BatchLaunch bl{};
+        uint32_t grid = 0, block = 0;
+        size_t smem = 0;
+    } kind[kBKinds];
 };
 
 namespace {
@@ -403,6 +441,9 @@ int alloc_common(snn_net *net)
     dn.flags = net->cfg.flags;
     dn.deriv_period = net->cfg.deriv_period_ms;
     dn.dense_rows = net->launch.dense_rows ? net->launch.dense_rows : 64;
+    dn.own_c0 = 0;
+    dn.own_c1 = dn.C;
+    dn.tile = 0;
     dn.dense_min_spikes = dense_threshold(net->N, net->launch.dense_permille);
     dn.deriv_bias = net->cfg.deriv_bias_q16;
     dn.deriv_decay = net->cfg.deriv_decay_q16;
@@ -423,7 +464,7 @@ int setup_dense(snn_net *net)
         // the column-ordered delivery: deliver_block threads per column, at
         // most deliver_blocks_per_sm resident blocks per SM (one wave)
         int per_sm = 0;
-        const uint32_t ob = net->launch.deliver_block;
+        const uint32_t ob = ordered_block(net->launch.deliver_block);
         const size_t obytes = ordered_smem_bytes(net->cfg.neurons_per_col, ob);
         SNN_CUDA(cudaFuncSetAttribute(k_deliver_ordered, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)obytes));
         SNN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_deliver_ordered, (int)ob, obytes));
@@ -433,7 +474,9 @@ int setup_dense(snn_net *net)
             net->ordered_grid = (int)std::min<int64_t>(net->dn.C, (int64_t)per_sm * net->sm_count);
         }
     }
-    if (net->cfg.neurons_per_col > kDenseMaxNpc) return SNN_OK;
+    // a tile takes the column-ordered delivery in every step (it alone
+    // delivers to the tile's own columns only)
+    if (net->cfg.neurons_per_col > kDenseMaxNpc || net->dn.tile) return SNN_OK;
     // both stage each depression amount in 15 bits
     std::vector<int32_t> lut;
     if (build_luts(&net->cfg, lut) != SNN_OK) return SNN_OK;
@@ -601,6 +644,7 @@ int cuda_init(snn_net *net, void *cuda_stream)
 {
     SNN_CUDA(cudaGetDevice(&net->device));
     SNN_CUDA(cudaDeviceGetAttribute(&net->sm_count, cudaDevAttrMultiProcessorCount, net->device));
+    SNN_TRY(noalloc_lookup(net->device, &net->noalloc_base));
     if (cuda_stream) {
         net->stream = (cudaStream_t)cuda_stream;
     } else {
@@ -694,8 +738,8 @@ void launch_step(snn_net *net, int32_t t, cudaStream_t s, bool exact_t)
     }
     mark(0);
     if (dn.ordered_ok)
-        k_deliver_ordered<<<net->ordered_grid, L.deliver_block, ordered_smem_bytes(dn.npc, L.deliver_block), s>>>(dn,
-                                                                                                           t_now);
+        k_deliver_ordered<<<net->ordered_grid, ordered_block(L.deliver_block),
+                            ordered_smem_bytes(dn.npc, ordered_block(L.deliver_block)), s>>>(dn, t_now);
     else k_deliver<<<g_del, L.deliver_block, 0, s>>>(dn, t_now);
     ++launched;
     if (dn.staged_ok) {
@@ -1140,6 +1184,59 @@ int snn_set_stimulus(snn_net *net, const snn_stimulus *host_events, size_t n)
     return set_stimulus_impl(net, host_events, n);
 }
 
+int snn_set_tile(snn_net *net, uint32_t first_col, uint32_t n_cols)
+{
+    if (!net) { set_error("net is NULL"); return SNN_EINVAL; }
+    const uint32_t C = net->dn.C;
+    if (n_cols == 0 || first_col >= C || n_cols > C - first_col) { set_error("column range outside the torus"); return SNN_EINVAL; }
+    if (net->t != 0) { set_error("a net becomes a tile before its first step"); return SNN_ESTATE; }
+    if (!net->tgt16 || !net->dn.ordered_ok) {
+        set_error("tiles need a generated net with compact targets");
+        return SNN_ESTATE;
+    }
+    const bool whole = first_col == 0 && n_cols == C;
+    if (!whole && !net->inject_buf) SNN_TRY(dalloc_t(net, (size_t)net->N, &net->inject_buf));
+    net->dn.own_c0 = first_col;
+    net->dn.own_c1 = first_col + n_cols;
+    net->dn.tile = whole ? 0 : 1;
+    net->dn.dense_min_spikes = dense_threshold(net->N, net->launch.dense_permille);
+    SNN_TRY(setup_dense(net));
+    if (!net->dense_ok) net->dn.dense_min_spikes = 0xffffffffu;
+    drop_graphs(net);
+    return SNN_OK;
+}
+
+int snn_inject_spikes(snn_net *net, const int32_t *host_gids, uint32_t n)
+{
+    if (!net) { set_error("net is NULL"); return SNN_EINVAL; }
+    if (!net->dn.tile) { set_error("spikes are injected into tiles only"); return SNN_ESTATE; }
+    if (net->t < 1) { set_error("no step has run yet"); return SNN_ESTATE; }
+    if (n == 0) return SNN_OK;
+    if (!host_gids) { set_error("host_gids is NULL"); return SNN_EINVAL; }
+    const uint32_t npc = net->dn.npc;
+    std::vector<uint8_t> seen;
+    for (uint32_t k = 0; k < n; ++k) {
+        const int32_t g = host_gids[k];
+        if (g < 0 || (uint32_t)g >= net->N) { set_error("gid %d out of range", g); return SNN_EINVAL; }
+        const uint32_t col = (uint32_t)g / npc;
+        if (col >= net->dn.own_c0 && col < net->dn.own_c1) {
+            set_error("gid %d belongs to the tile itself", g);
+            return SNN_EINVAL;
+        }
+    }
+    if (n > net->N) { set_error("more spikes than neurons"); return SNN_EINVAL; }
+    seen.assign(net->N, 0);
+    for (uint32_t k = 0; k < n; ++k) {
+        if (seen[(uint32_t)host_gids[k]]) { set_error("gid %d appears twice", host_gids[k]); return SNN_EINVAL; }
+        seen[(uint32_t)host_gids[k]] = 1;
+    }
+    SNN_CUDA(cudaMemcpyAsync(net->inject_buf, host_gids, (size_t)n * 4, cudaMemcpyHostToDevice, net->stream));
+    k_inject<<<1, 1024, 0, net->stream>>>(net->dn, net->t - 1, net->inject_buf, n);
+    SNN_CUDA(cudaGetLastError());
+    SNN_CUDA(cudaStreamSynchronize(net->stream));
+    return SNN_OK;
+}
+
 int snn_set_thalamic(snn_net *net, int on)
 {
     if (!net) { set_error("net is NULL"); return SNN_EINVAL; }
@@ -1233,6 +1330,7 @@ void snn_batch_free(snn_batch *b)
     if (!b) return;
     if (b->main) cudaStreamSynchronize(b->main);
     if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->tables) cudaFree(b->tables);
     for (cudaEvent_t e : b->join) cudaEventDestroy(e);
     if (b->fork) cudaEventDestroy(b->fork);
     for (cudaStream_t st : b->branch) cudaStreamDestroy(st);
@@ -1258,6 +1356,13 @@ int snn_batch_create(snn_net *const *nets, uint32_t n_nets, uint32_t graph_steps
     auto fail = [&](int code) { snn_batch_free(b); return code; };
     b->nets.assign(nets, nets + n_nets);
     b->L = (graph_steps ? graph_steps : 10) & ~1u;
+    b->device = dev;
+    b->launch = nets[0]->launch;
+    b->launch.graph_steps = b->L;
+    if (cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        set_error("cudaDeviceGetAttribute failed");
+        return fail(SNN_ECUDA);
+    }
     if (cudaStreamCreateWithFlags(&b->main, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) {
         set_error("stream / event creation failed");
@@ -1279,8 +1384,8 @@ int snn_batch_create(snn_net *const *nets, uint32_t n_nets, uint32_t graph_steps
 namespace {
 
 // the next `count` steps of every net (from its own t), each net on its own
-// branch stream, joined back into the batch's main stream (captured into a
-// graph, or run eagerly)
+// branch stream, joined back into the batch's main stream (single eager
+// steps that do not fill a captured chunk)
 void batch_enqueue(snn_batch *b, uint32_t count, bool exact_t)
 {
     cudaEventRecord(b->fork, b->main);
@@ -1293,15 +1398,231 @@ void batch_enqueue(snn_batch *b, uint32_t count, bool exact_t)
     }
 }
 
+// blocks of every net in one batched launch of a kind: as many as the net
+// would use alone (one resident wave, at most `cap`), so that whichever nets
+// have work in a step (the device decides per net and step) can fill the
+// GPU; the blocks of a net with nothing to do return at once.  Nets the
+// kind does not apply to get none (weight 0).
+void share_blocks(const std::vector<double> &weight, const std::vector<uint64_t> &cap, uint64_t wave,
+                  std::vector<uint32_t> &cnt)
+{
+    cnt.assign(weight.size(), 0);
+    for (size_t i = 0; i < weight.size(); ++i) {
+        if (weight[i] <= 0) continue;
+        const uint64_t c = std::max<uint64_t>(1, std::min<uint64_t>(wave, std::max<uint64_t>(1, cap[i])));
+        cnt[i] = (uint32_t)std::min<uint64_t>(c, 1u << 20);
+    }
+}
+
+// resident blocks per SM of a batched kernel (at least 1), capped at `cap`
+int batch_occupancy(const void *kernel, uint32_t block, size_t smem, uint32_t cap)
+{
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, (int)block, smem) != cudaSuccess) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    return std::max(1, std::min<int>(per_sm, (int)std::max(1u, cap)));
+}
+
+// the launch tables of every kind for the nets as they are now (DevNet
+// copies, parities), uploaded to the batch's device buffer
+int batch_tables(snn_batch *b)
+{
+    const size_t nn = b->nets.size();
+    const snn_launch &L = b->launch;
+    const uint64_t sms = (uint64_t)std::max(1, b->sm_count);
+    std::vector<uint32_t> cnt[kBKinds];
+    for (int k = 0; k < kBKinds; ++k) b->kind[k] = snn_batch::Kind{};
+    std::vector<double> w(nn);
+    std::vector<uint64_t> cap(nn);
+    auto work = [&](size_t i) { return (double)b->nets[i]->N * (double)std::max<int64_t>(1, b->nets[i]->S / std::max<uint32_t>(1, b->nets[i]->N)); };
+    int optin = 0;
+    SNN_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device));
+    // potentiation: warp per spiker
+    for (size_t i = 0; i < nn; ++i) {
+        const snn_net *n = b->nets[i];
+        w[i] = (n->cfg.flags & SNN_STDP_OFF) ? 0.0 : work(i);
+        cap[i] = (n->N + L.ltp_block / 32 - 1) / (L.ltp_block / 32);
+    }
+    b->kind[kBLtp].block = L.ltp_block;
+    share_blocks(w, cap, sms * batch_occupancy((const void *)k_ltp_b, L.ltp_block, 0, L.ltp_blocks_per_sm), cnt[kBLtp]);
+    // fold and long-term update (return at once off period ends)
+    for (size_t i = 0; i < nn; ++i) {
+        const snn_net *n = b->nets[i];
+        w[i] = n->cfg.deriv_period_ms ? (double)std::max<int64_t>(1, n->n_rin) : 0.0;
+        cap[i] = (n->N + 63) / 64;
+    }
+    b->kind[kBFold].block = 256;
+    share_blocks(w, cap, sms * 8, cnt[kBFold]);
+    for (size_t i = 0; i < nn; ++i) {
+        const snn_net *n = b->nets[i];
+        w[i] = n->cfg.deriv_period_ms ? work(i) : 0.0;
+        cap[i] = ((uint64_t)n->dn.C * n->dn.ne + L.deriv_block / 32 - 1) / (L.deriv_block / 32);
+    }
+    b->kind[kBDeriv].block = L.deriv_block;
+    share_blocks(w, cap, sms * 8, cnt[kBDeriv]);
+    // deliveries: column-ordered (compact nets), ring order (the others),
+    // column-staged (nets where it may run)
+    size_t smem_o = 0, smem_s = 0, smem_d = 0;
+    for (size_t i = 0; i < nn; ++i) {
+        const snn_net *n = b->nets[i];
+        w[i] = n->dn.ordered_ok ? work(i) : 0.0;
+        cap[i] = n->dn.C;
+        if (n->dn.ordered_ok) smem_o = std::max(smem_o, ordered_smem_bytes(n->dn.npc, ordered_block(L.deliver_block)));
+    }
+    b->kind[kBOrdered].block = ordered_block(L.deliver_block);
+    b->kind[kBOrdered].smem = smem_o;
+    if (smem_o) {
+        if (smem_o + 1024 > (size_t)optin) { set_error("batch: ordered delivery needs too much shared memory"); return SNN_EINVAL; }
+        SNN_CUDA(cudaFuncSetAttribute(k_deliver_ordered_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_o));
+    }
+    share_blocks(w, cap, sms * batch_occupancy((const void *)k_deliver_ordered_b, ordered_block(L.deliver_block), smem_o,
+                                               L.deliver_blocks_per_sm), cnt[kBOrdered]);
+    for (size_t i = 0; i < nn; ++i) {
+        const snn_net *n = b->nets[i];
+        w[i] = n->dn.ordered_ok ? 0.0 : work(i);
+        cap[i] = ((uint64_t)n->N * n->dn.D / 4 + L.deliver_block - 1) / L.deliver_block;
+    }
+    b->kind[kBRing].block = L.deliver_block;
+    share_blocks(w, cap, sms * batch_occupancy((const void *)k_deliver_b, L.deliver_block, 0, L.deliver_blocks_per_sm),
+                 cnt[kBRing]);
+    for (size_t i = 0; i < nn; ++i) {
+        const snn_net *n = b->nets[i];
+        w[i] = n->dn.staged_ok ? work(i) : 0.0;
+        cap[i] = n->dn.C;
+        if (n->dn.staged_ok) smem_s = std::max(smem_s, staged_smem_bytes(n->dn.npc, kStagedBlock));
+    }
+    b->kind[kBStaged].block = kStagedBlock;
+    b->kind[kBStaged].smem = smem_s;
+    if (smem_s) {
+        if (smem_s + 1024 > (size_t)optin) { set_error("batch: staged delivery needs too much shared memory"); return SNN_EINVAL; }
+        SNN_CUDA(cudaFuncSetAttribute(k_deliver_cols_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_s));
+    }
+    share_blocks(w, cap, sms * batch_occupancy((const void *)k_deliver_cols_b, kStagedBlock, smem_s, 64), cnt[kBStaged]);
+    // dense pass (nets where it may run), work units of dense_rows rows
+    for (size_t i = 0; i < nn; ++i) {
+        const snn_net *n = b->nets[i];
+        w[i] = n->dense_ok ? (double)n->S : 0.0;
+        cap[i] = (uint64_t)n->dn.C * ((n->dn.npc + n->dn.dense_rows - 1) / std::max(1u, n->dn.dense_rows));
+        if (n->dense_ok) smem_d = std::max(smem_d, dense_smem_bytes(n->dn.npc, L.dense_block));
+    }
+    b->kind[kBDense].block = L.dense_block;
+    b->kind[kBDense].smem = smem_d;
+    if (smem_d) {
+        if (smem_d + 1024 > (size_t)optin) { set_error("batch: dense pass needs too much shared memory"); return SNN_EINVAL; }
+        SNN_CUDA(cudaFuncSetAttribute(k_dense_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_d));
+    }
+    share_blocks(w, cap, sms * batch_occupancy((const void *)k_dense_b, L.dense_block, smem_d, 64), cnt[kBDense]);
+    // neuron update and probes: exact block counts
+    for (int k : {kBNeuron32, kBNeuron64, kBProbe}) cnt[k].assign(nn, 0);
+    for (size_t i = 0; i < nn; ++i) {
+        const snn_net *n = b->nets[i];
+        const uint32_t nb = (n->N + L.neuron_block * kNeuronsPerThread - 1) / (L.neuron_block * kNeuronsPerThread);
+        cnt[n->dn.vd ? kBNeuron64 : kBNeuron32][i] = nb;
+        cnt[kBProbe][i] = (n->dn.probe_n + 255) / 256;
+    }
+    b->kind[kBNeuron32].block = b->kind[kBNeuron64].block = L.neuron_block;
+    b->kind[kBProbe].block = 256;
+    // one device buffer: DevNet[nn], parity[nn], then per kind first[nn],
+    // count[nn] and net_of[grid]
+    size_t bytes = ((nn * sizeof(DevNet) + nn + 255) & ~size_t(255));
+    size_t off_kind[kBKinds];
+    for (int k = 0; k < kBKinds; ++k) {
+        uint64_t grid = 0;
+        for (uint32_t c : cnt[k]) grid += c;
+        if (grid > 0x7fffffffull) { set_error("batch: too many blocks"); return SNN_EINVAL; }
+        b->kind[k].grid = (uint32_t)grid;
+        off_kind[k] = bytes;
+        bytes += ((2 * nn + grid) * 4 + 255) & ~size_t(255);
+    }
+    std::vector<uint8_t> host(bytes, 0);
+    DevNet *hn = reinterpret_cast<DevNet *>(host.data());
+    uint8_t *hp = host.data() + nn * sizeof(DevNet);
+    for (size_t i = 0; i < nn; ++i) {
+        hn[i] = b->nets[i]->dn;
+        hp[i] = (uint8_t)(b->nets[i]->t & 1);
+    }
+    // every net's blocks are contiguous; nets with the most synapses come
+    // first, so that the longest work starts first
+    std::vector<size_t> order(nn);
+    for (size_t i = 0; i < nn; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return work(x) > work(y); });
+    for (int k = 0; k < kBKinds; ++k) {
+        uint32_t *first = reinterpret_cast<uint32_t *>(host.data() + off_kind[k]);
+        uint32_t *count = first + nn;
+        uint32_t *net_of = count + nn;
+        uint32_t acc = 0;
+        for (size_t i : order) {
+            first[i] = acc;
+            count[i] = cnt[k][i];
+            for (uint32_t c = 0; c < cnt[k][i]; ++c) net_of[acc + c] = (uint32_t)i;
+            acc += cnt[k][i];
+        }
+    }
+    if (bytes > b->tables_bytes) {
+        if (b->tables) cudaFree(b->tables);
+        b->tables = nullptr;
+        b->tables_bytes = 0;
+        cudaError_t e = cudaMalloc(&b->tables, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            set_error("batch tables: cudaMalloc(%zu) failed", bytes);
+            return SNN_ENOMEM;
+        }
+        b->tables_bytes = bytes;
+    }
+    SNN_CUDA(cudaMemcpyAsync(b->tables, host.data(), bytes, cudaMemcpyHostToDevice, b->main));
+    SNN_CUDA(cudaStreamSynchronize(b->main));
+    uint8_t *base = reinterpret_cast<uint8_t *>(b->tables);
+    for (int k = 0; k < kBKinds; ++k) {
+        BatchLaunch &bl = b->kind[k].bl;
+        bl.nets = reinterpret_cast<const DevNet *>(base);
+        bl.parity = base + nn * sizeof(DevNet);
+        bl.first = reinterpret_cast<const uint32_t *>(base + off_kind[k]);
+        bl.count = bl.first + nn;
+        bl.net_of = bl.count + nn;
+        bl.k = 0;
+    }
+    return SNN_OK;
+}
+
+// one step (index k of the chunk) of every net: each kind of kernel once
+void batch_launch_step(snn_batch *b, uint32_t k)
+{
+    cudaStream_t s = b->main;
+    auto go = [&](int kind, auto kernel) {
+        const snn_batch::Kind &x = b->kind[kind];
+        if (!x.grid) return;
+        BatchLaunch bl = x.bl;
+        bl.k = k;
+        kernel<<<x.grid, x.block, x.smem, s>>>(bl);
+    };
+    // [S4(t-1) S5(t-1) S1(t)] then [S2(t) S3(t)], as launch_step
+    go(kBLtp, k_ltp_b);
+    go(kBFold, k_fold_b);
+    go(kBDeriv, k_deriv_b);
+    go(kBOrdered, k_deliver_ordered_b);
+    go(kBRing, k_deliver_b);
+    go(kBStaged, k_deliver_cols_b);
+    go(kBDense, k_dense_b);
+    go(kBNeuron32, k_neuron_f32_b);
+    go(kBNeuron64, k_neuron_f64_b);
+    go(kBProbe, k_probe_b);
+}
+
+// a chunk of L steps of every net as one graph: per step one launch per kind
+// of kernel for the whole batch
 int batch_capture(snn_batch *b)
 {
     if (b->graph) {
         cudaGraphExecDestroy(b->graph);
         b->graph = nullptr;
     }
+    SNN_TRY(batch_tables(b));
     cudaGraph_t g = nullptr;
     SNN_CUDA(cudaStreamBeginCapture(b->main, cudaStreamCaptureModeThreadLocal));
-    batch_enqueue(b, b->L, false);
+    for (uint32_t k = 0; k < b->L; ++k) batch_launch_step(b, k);
     cudaError_t e = cudaStreamEndCapture(b->main, &g);
     if (e != cudaSuccess) { set_error("batch capture failed: %s", cudaGetErrorString(e)); return SNN_ECUDA; }
     e = cudaGraphInstantiate(&b->graph, g, 0);
@@ -1364,6 +1685,87 @@ int snn_batch_run(snn_batch *b, uint32_t n_ms)
         }
     }
     return rc;
+}
+
+int snn_batch_set_launch(snn_batch *b, const snn_launch *launch)
+{
+    if (!b || !launch) { set_error("NULL argument"); return SNN_EINVAL; }
+    snn_launch L = b->launch;
+    auto pick = [](uint32_t v, uint32_t cur) { return v ? v : cur; };
+    L.deliver_block = pick(launch->deliver_block, L.deliver_block);
+    L.deliver_blocks_per_sm = pick(launch->deliver_blocks_per_sm, L.deliver_blocks_per_sm);
+    L.neuron_block = pick(launch->neuron_block, L.neuron_block);
+    L.ltp_block = pick(launch->ltp_block, L.ltp_block);
+    L.ltp_blocks_per_sm = pick(launch->ltp_blocks_per_sm, L.ltp_blocks_per_sm);
+    L.deriv_block = pick(launch->deriv_block, L.deriv_block);
+    L.dense_block = pick(launch->dense_block, L.dense_block);
+    L.graph_steps = pick(launch->graph_steps, L.graph_steps);
+    for (uint32_t x : {L.deliver_block, L.neuron_block, L.ltp_block, L.deriv_block, L.dense_block}) {
+        if (x < 32 || x > 1024 || x % 32) { set_error("block sizes must be multiples of 32 in 32..1024"); return SNN_EINVAL; }
+    }
+    if (L.deliver_blocks_per_sm > 64 || L.ltp_blocks_per_sm > 64) { set_error("blocks per SM must be <= 64"); return SNN_EINVAL; }
+    if (L.graph_steps < 2) { set_error("a batch needs graph_steps >= 2"); return SNN_EINVAL; }
+    b->launch = L;
+    b->L = L.graph_steps & ~1u;
+    b->launch.graph_steps = b->L;
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    return SNN_OK;
+}
+
+int snn_batch_get_launch(const snn_batch *b, snn_launch *launch)
+{
+    if (!b || !launch) { set_error("NULL argument"); return SNN_EINVAL; }
+    *launch = b->launch;
+    return SNN_OK;
+}
+
+int snn_batch_autotune(snn_batch *b, uint32_t probe_ms, snn_launch *best)
+{
+    if (!b) { set_error("batch is NULL"); return SNN_EINVAL; }
+    for (snn_net *n : b->nets)
+        if (n->explicit_net) { set_error("autotuning restarts the nets: generated nets only"); return SNN_ESTATE; }
+    if (probe_ms == 0) probe_ms = 50;
+    const snn_launch base = b->launch;
+    std::vector<snn_launch> cand;
+    for (uint32_t db : {128u, 256u})
+        for (uint32_t bps : {4u, 8u})
+            for (uint32_t gs : {10u, 50u}) {
+                snn_launch c = base;
+                c.deliver_block = db;
+                c.deliver_blocks_per_sm = bps;
+                c.ltp_blocks_per_sm = bps;
+                c.graph_steps = gs;
+                cand.push_back(c);
+            }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    SNN_CUDA(cudaEventCreate(&e0));
+    SNN_CUDA(cudaEventCreate(&e1));
+    float best_ms = 1e30f;
+    size_t best_i = 0;
+    int rc = SNN_OK;
+    for (size_t i = 0; i < cand.size() && rc == SNN_OK; ++i) {
+        if ((rc = snn_batch_set_launch(b, &cand[i])) != SNN_OK) break;
+        for (snn_net *n : b->nets)
+            if ((rc = snn_reset(n)) != SNN_OK) break;
+        if (rc != SNN_OK) break;
+        cudaEventRecord(e0, b->main);
+        if ((rc = snn_batch_run(b, probe_ms)) != SNN_OK) break;
+        cudaEventRecord(e1, b->main);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) { best_ms = ms; best_i = i; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != SNN_OK) return rc;
+    SNN_TRY(snn_batch_set_launch(b, &cand[best_i]));
+    for (snn_net *n : b->nets) SNN_TRY(snn_reset(n));
+    if (best) *best = b->launch;
+    return SNN_OK;
 }
 
 int snn_autotune(snn_net *net, uint32_t probe_ms, snn_launch *best)
@@ -1556,26 +1958,10 @@ int snn_read_synapses_noalloc(snn_net *net, uint32_t first, uint32_t count, int3
         return SNN_EINVAL;
     }
     if (total == 0) return SNN_OK;
-    // device address of the staging array, once per device, with that device current
-    if (net->device < 0 || net->device >= kMaxDevices) { set_error("device ordinal too large"); return SNN_EINVAL; }
-    int32_t *base = nullptr;
-    {
-        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-        if (!g_noalloc_ptr[net->device]) {
-            int prev = 0;
-            SNN_CUDA(cudaGetDevice(&prev));
-            if (prev != net->device) SNN_CUDA(cudaSetDevice(net->device));
-            void *ptr = nullptr;
-            const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-            if (prev != net->device) cudaSetDevice(prev);
-            if (e != cudaSuccess) {
-                set_error("cudaGetSymbolAddress of the staging array failed: %s", cudaGetErrorString(e));
-                return SNN_ECUDA;
-            }
-            g_noalloc_ptr[net->device] = (int32_t *)ptr;
-        }
-        base = g_noalloc_ptr[net->device];
-    }
+    // device address of the staging array, looked up when the net was set
+    // up on its device (with that device current)
+    int32_t *base = net->noalloc_base;
+    if (!base) { set_error("no staging address for this net's device"); return SNN_ECUDA; }
     SNN_TRY(flush_owed(net));
     const size_t M = SNN_NOALLOC_MAX_SYNAPSES;
     int32_t *dt = host_tgt ? base : nullptr;

@@ -165,7 +165,7 @@ __device__ __forceinline__ void dense_row_walk(const DevNet &n, int64_t base, in
     }
 }
 
-__global__ void __launch_bounds__(1024) k_dense(DevNet n, const int *t_now)
+__device__ __forceinline__ void dense_body(const DevNet &n, const int *t_now, const Part &g)
 {
     extern __shared__ int4 smem_i4[];
     const int t = *t_now;
@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(1024) k_dense(DevNet n, const int *t_now)
         s_lutp[i] = n.lut_p[i];
         s_lutm[i] = n.lut_m[i];
     }
-    drive(n, t, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+    drive(n, t, part_tid(g), part_threads(g));
     int32_t *w_off = s_off + warp * 32;
     int32_t *w_amt = s_amt + warp * 32;
     const int D = (int)n.D;
@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(1024) k_dense(DevNet n, const int *t_now)
     // the grid is at most one wave of resident blocks; a block takes work
     // units (a column and a chunk of its rows) from a step-wide cursor
     __shared__ uint32_t s_unit;
-    for (uint32_t unit = blockIdx.x; unit < n.C * chunks;) {
+    for (uint32_t unit = g.bid; unit < n.C * chunks;) {
         const uint32_t col = unit / chunks;
         const uint32_t r0 = (unit - col * chunks) * n.dense_rows;
         const uint32_t r1 = min(npc, r0 + n.dense_rows);
@@ -317,7 +317,7 @@ __global__ void __launch_bounds__(1024) k_dense(DevNet n, const int *t_now)
                 if (v) red_add(&dst[loc], v);
             }
         }
-        if (threadIdx.x == 0) s_unit = gridDim.x + atomicAdd(&n.ctr->dense_cursor, 1u);
+        if (threadIdx.x == 0) s_unit = g.nblk + atomicAdd(&n.ctr->dense_cursor, 1u);
         __syncthreads();
         unit = s_unit;
     }
@@ -331,7 +331,7 @@ __global__ void __launch_bounds__(1024) k_dense(DevNet n, const int *t_now)
             atomicAdd(&n.ctr->dense_e_all, ba);
             atomicAdd(&n.ctr->dense_e_exc, be);
         }
-        if (blockIdx.x == 0) {
+        if (g.bid == 0) {
             // potentiation visits: every incoming excitatory synapse of the
             // neurons that fired at t - 1 (counted when those spikes closed)
             if (ltp_on) n.ctr->dense_l_exc += n.ctr->l_exc_last;
@@ -339,6 +339,15 @@ __global__ void __launch_bounds__(1024) k_dense(DevNet n, const int *t_now)
             if (deriv_on) n.ctr->dense_deriv_steps += 1;
         }
     }
+}
+
+__global__ void __launch_bounds__(1024) k_dense(DevNet n, const int *t_now) { dense_body(n, t_now, whole_grid()); }
+
+__global__ void __launch_bounds__(1024) k_dense_b(BatchLaunch b)
+{
+    const BatchBlock x = batch_block(b);
+    const DevNet n = b.nets[x.net];
+    dense_body(n, x.t_now, x.part);
 }
 
 }  // namespace snn

@@ -102,6 +102,42 @@ struct DevNet {
     uint32_t deriv_period;
     uint32_t dense_min_spikes;       // spikes of step t-1 from which step t takes the dense pass
     uint32_t dense_rows;             // source rows per block of the dense pass
+    // a tile of a torus partitioned by columns (Sec. 2 "Delivery of spiking
+    // messages"): the net integrates and delivers to the neurons of columns
+    // [own_c0, own_c1) only; the spikes of the other columns arrive from their
+    // owners (snn_inject_spikes).  A whole net owns every column (tile = 0).
+    uint32_t own_c0, own_c1;
+    int tile;
+};
+
+__device__ __forceinline__ bool owned_column(const DevNet &n, uint32_t col)
+{
+    return col >= n.own_c0 && col < n.own_c1;
+}
+
+// The blocks among which one net's share of a launch is split: the whole
+// grid of a single-net launch, or the net's range of blocks in a launch that
+// steps every net of a batch.  Kernels index their work by (bid, nblk)
+// instead of (blockIdx.x, gridDim.x).
+struct Part {
+    uint32_t bid, nblk;
+};
+
+__device__ __forceinline__ Part whole_grid() { return Part{blockIdx.x, gridDim.x}; }
+__device__ __forceinline__ uint32_t part_tid(const Part &g) { return g.bid * blockDim.x + threadIdx.x; }
+__device__ __forceinline__ uint32_t part_threads(const Part &g) { return g.nblk * blockDim.x; }
+
+// One launch of a kind of step kernel for every net of a batch: block b
+// works for net net_of[b] as block b - first[net] of count[net] (a net's
+// blocks are contiguous); the net's step t has parity (parity[net] + k) & 1,
+// k being the step's index in the captured chunk of steps.
+struct BatchLaunch {
+    const DevNet *nets;              // [n_nets]
+    const uint32_t *first;           // [n_nets] first block of every net
+    const uint32_t *count;           // [n_nets] blocks of every net
+    const uint32_t *net_of;          // [grid] net of every block
+    const uint8_t *parity;           // [n_nets] parity of every net's step at the chunk's start
+    uint32_t k;                      // step of the chunk
 };
 
 // ---------------------------------------------------------------------------
@@ -405,10 +441,50 @@ __global__ void k_probe(DevNet n, const int *t_now);
 __global__ void k_ltp(DevNet n, const int *t_now, int force);
 __global__ void k_deriv(DevNet n, const int *t_now, int force);
 __global__ void k_fold(DevNet n, const int *t_now, int force);
+__global__ void k_inject(DevNet n, int t, const int32_t *gid, uint32_t count);
+
+// the same kernels for every net of a batch in one launch (BatchLaunch)
+__global__ void k_deliver_b(BatchLaunch b);
+__global__ void k_dense_b(BatchLaunch b);
+__global__ void k_deliver_cols_b(BatchLaunch b);
+__global__ void k_deliver_ordered_b(BatchLaunch b);
+__global__ void k_neuron_f32_b(BatchLaunch b);
+__global__ void k_neuron_f64_b(BatchLaunch b);
+__global__ void k_probe_b(BatchLaunch b);
+__global__ void k_ltp_b(BatchLaunch b);
+__global__ void k_deriv_b(BatchLaunch b);
+__global__ void k_fold_b(BatchLaunch b);
+
+// net, part and step slots of a block of a batched launch
+struct BatchBlock {
+    uint32_t net;
+    Part part;
+    const int *t_now;
+    int *t_next;
+};
+
+__device__ __forceinline__ BatchBlock batch_block(const BatchLaunch &b)
+{
+    BatchBlock x;
+    x.net = b.net_of[blockIdx.x];
+    x.part = Part{blockIdx.x - b.first[x.net], b.count[x.net]};
+    const int par = (int)((b.parity[x.net] + b.k) & 1u);
+    x.t_now = &b.nets[x.net].ctr->t_slot[par];
+    x.t_next = &b.nets[x.net].ctr->t_slot[par ^ 1];
+    return x;
+}
 
 size_t dense_smem_bytes(uint32_t npc, uint32_t block);
 size_t staged_smem_bytes(uint32_t npc, uint32_t block);
 size_t ordered_smem_bytes(uint32_t npc, uint32_t block);
 constexpr uint32_t kStagedBlock = 512;      // threads per block of the column-staged delivery
+// the column-ordered delivery is compiled for five resident blocks of at most
+// this many threads per SM (47 registers; the measured optimum): a launch
+// shape asking for more threads per block is clamped to it
+constexpr uint32_t kOrderedMaxBlock = 256;
+__host__ __device__ __forceinline__ uint32_t ordered_block(uint32_t deliver_block)
+{
+    return deliver_block < kOrderedMaxBlock ? deliver_block : kOrderedMaxBlock;
+}
 
 }  // namespace snn

@@ -42,7 +42,7 @@ namespace snn {
 // reduction and, on plastic synapses, subtract the LTD amount at lag
 // t - last_spike[target].
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_deliver(DevNet n, const int *t_now)
+__device__ __forceinline__ void deliver_ring(const DevNet &n, const int *t_now, const Part &g)
 {
     __shared__ int32_t s_lut[kLut];
     __shared__ int s_start[2 * 32 + 1];
@@ -74,8 +74,8 @@ __global__ void __launch_bounds__(1024) k_deliver(DevNet n, const int *t_now)
         s_start[nl] = acc;
     }
     __syncthreads();
-    const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x;
-    const uint32_t gthreads = gridDim.x * blockDim.x;
+    const uint32_t gtid = part_tid(g);
+    const uint32_t gthreads = part_threads(g);
     drive(n, t, gtid, gthreads);
 
     const int total = s_start[nl];
@@ -219,10 +219,10 @@ size_t ordered_smem_bytes(uint32_t npc, uint32_t block)
 // s_hist: the history words (bit k: fired at t - k) of the column's rows.
 template <bool kStage>
 __device__ __forceinline__ void deliver_cols(const DevNet &n, int t, int32_t *s_lut, int32_t *s_in, int32_t *s_tile,
-                                             void *s_amt, uint32_t *s_hist)
+                                             void *s_amt, uint32_t *s_hist, const Part &g)
 {
     __shared__ uint32_t s_col[kSlots];
-    __shared__ uint32_t s_unit;
+    __shared__ uint32_t s_unit[2];             // the next column, claimed while this one is walked
     __shared__ uint32_t s_grp;                 // row groups of the current column handed out
     uint16_t *s_x = reinterpret_cast<uint16_t *>(s_amt);
     int32_t *s_ltd = reinterpret_cast<int32_t *>(s_amt);
@@ -232,7 +232,7 @@ __device__ __forceinline__ void deliver_cols(const DevNet &n, int t, int32_t *s_
     const bool deliver_on = !(n.flags & SNN_DELIVERY_OFF);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < kLut; i += blockDim.x) s_lut[i] = n.lut_m[i];
-    drive(n, t, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+    drive(n, t, part_tid(g), part_threads(g));
     const int D = (int)n.D;
     const uint32_t dmask_e = (2u << D) - 2u, dmask_i = (2u << n.D_inh) - 2u;
     int32_t *w_c0 = s_tile + warp * kTileWords;                // [32] first chunk (column-relative)
@@ -242,16 +242,47 @@ __device__ __forceinline__ void deliver_cols(const DevNet &n, int t, int32_t *s_
     int32_t *w_exc = w_b + 32;                                 // [32] 1: excitatory row
     uint32_t *w_items = reinterpret_cast<uint32_t *>(w_exc + 32);   // [kItemCap] pending items
     unsigned long long ev_all = 0, ev_exc = 0;
-    for (uint32_t col = blockIdx.x; col < n.C;) {
+    uint32_t par = 0;
+    for (uint32_t col = g.bid; col < n.C; par ^= 1u) {
         if (threadIdx.x < kSlots) s_col[threadIdx.x] = (uint32_t)n.nbr[col * kSlotStride + threadIdx.x];
-        if (threadIdx.x == 0) s_grp = 0;
+        if (threadIdx.x == 0) {
+            s_grp = 0;
+            s_unit[par] = g.nblk + atomicAdd(&n.ctr->staged_cursor, 1u);
+        }
         if (kStage) __syncthreads();
         // one round of loads for the whole column: history words, and the
         // staged neurons' last spikes turned into LTD amounts at lag
         // t - last_spike >= 1 (saturated at the table end, whose entry is 0)
-        for (uint32_t loc = threadIdx.x; loc < npc; loc += blockDim.x)
-            s_hist[loc] = deliver_on ? n.hl[col * npc + loc].x : 0u;
-        if (kStage) {
+        if (!kStage) {
+            constexpr int kSetup = 8;                  // rows per thread in flight
+            const int32_t *ls = n.last_spike + (size_t)col * npc;
+            const uint2 *hl = n.hl + (size_t)col * npc;
+            for (uint32_t base = threadIdx.x; base < npc; base += kSetup * blockDim.x) {
+                uint32_t hv[kSetup];
+                int32_t lv[kSetup];
+#pragma unroll
+                for (int q = 0; q < kSetup; ++q) {
+                    const uint32_t loc = base + q * blockDim.x;
+                    hv[q] = 0;
+                    lv[q] = kNever;
+                    if (loc < npc) {
+                        if (deliver_on) hv[q] = hl[loc].x;
+                        lv[q] = ls[loc];
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < kSetup; ++q) {
+                    const uint32_t loc = base + q * blockDim.x;
+                    if (loc < npc) {
+                        s_hist[loc] = hv[q];
+                        s_ltd[loc] = stdp ? s_lut[min(t - lv[q], kLut - 1)] : 0;
+                        s_in[loc] = 0;
+                    }
+                }
+            }
+        } else {
+            for (uint32_t loc = threadIdx.x; loc < npc; loc += blockDim.x)
+                s_hist[loc] = deliver_on ? n.hl[col * npc + loc].x : 0u;
             // at most 15 bits per amount: the host checks the table
             for (int sl = 0; sl < kSlots; ++sl) {
                 const int32_t *ls = n.last_spike + (size_t)s_col[sl] * npc;
@@ -261,12 +292,6 @@ __device__ __forceinline__ void deliver_cols(const DevNet &n, int t, int32_t *s_
                     x_row[loc] = stdp ? (uint16_t)s_lut[min(t - ls[loc], kLut - 1)] : (uint16_t)0;
                     in_row[loc] = 0;
                 }
-            }
-        } else {
-            const int32_t *ls = n.last_spike + (size_t)col * npc;
-            for (uint32_t loc = threadIdx.x; loc < npc; loc += blockDim.x) {
-                s_ltd[loc] = stdp ? s_lut[min(t - ls[loc], kLut - 1)] : 0;
-                s_in[loc] = 0;
             }
         }
         __syncthreads();
@@ -303,8 +328,10 @@ __device__ __forceinline__ void deliver_cols(const DevNet &n, int t, int32_t *s_
             w_exc[lane] = exc;
             if (lane == 0) {
                 w_start[32] = total;
-                ev_all += (unsigned long long)len_all;
-                ev_exc += (unsigned long long)len_exc;
+                if (!n.tile) {                 // a tile counts the events on its own columns below
+                    ev_all += (unsigned long long)len_all;
+                    ev_exc += (unsigned long long)len_exc;
+                }
             }
             __syncwarp();
             int j = 0;
@@ -326,6 +353,7 @@ __device__ __forceinline__ void deliver_cols(const DevNet &n, int t, int32_t *s_
                 }
                 const uint32_t tw[4] = {tv.x, tv.y, tv.z, tv.w};
                 const int32_t wk[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+                int tile_ev = 0;                                    // tiles: events on own columns
                 int32_t am[8];                                      // LTD amount, or (remote) last spike
                 uint32_t remote = 0;                                // bit u: target on another column
 #pragma unroll
@@ -340,18 +368,24 @@ __device__ __forceinline__ void deliver_cols(const DevNet &n, int t, int32_t *s_
                     } else {
                         const uint32_t slot = __umulhi(v, n.npc_recip);
                         const uint32_t loc = v - slot * npc;
+                        if (n.tile && !owned_column(n, s_col[slot])) continue;   // another tile's target
+                        if (n.tile) ++tile_ev;
                         if (slot == 0) {
                             atomicAdd(&s_in[loc], wk[u]);
                             am[u] = (ex && stdp) ? s_ltd[loc] : 0;
                         } else {
-                            const uint32_t g = s_col[slot] * npc + loc;          // target gid
-                            red_add(&n.I[g], wk[u]);
+                            const uint32_t gid = s_col[slot] * npc + loc;        // target gid
+                            red_add(&n.I[gid], wk[u]);
                             if (ex && stdp) {
-                                am[u] = n.last_spike[g];
+                                am[u] = n.last_spike[gid];
                                 remote |= 1u << u;
                             }
                         }
                     }
+                }
+                if (n.tile) {
+                    ev_all += (unsigned long long)tile_ev;
+                    if (ex) ev_exc += (unsigned long long)tile_ev;
                 }
                 if (ex && stdp) {
 #pragma unroll
@@ -393,14 +427,14 @@ __device__ __forceinline__ void deliver_cols(const DevNet &n, int t, int32_t *s_
                 td = (int)(it & 31u);
                 tv = lane < take;
             } else if (groups_left) {
-                uint32_t g = 0;
-                if (lane == 0) g = atomicAdd(&s_grp, 1u);
-                g = __shfl_sync(0xffffffffu, g, 0);
-                if (g >= ngroups) {
+                uint32_t grp = 0;
+                if (lane == 0) grp = atomicAdd(&s_grp, 1u);
+                grp = __shfl_sync(0xffffffffu, grp, 0);
+                if (grp >= ngroups) {
                     groups_left = false;
                     continue;
                 }
-                r = (ngroups - 1u - g) * 32u + lane;   // the last groups (inhibitory rows) first
+                r = (ngroups - 1u - grp) * 32u + lane;   // the last groups (inhibitory rows) first
                 uint32_t f = 0;                        // bit d: the row's source fired at t - d
                 if (r < npc) f = (s_hist[r] << 1) & (r < n.ne ? dmask_e : dmask_i);
                 const int mine = __popc(f);
@@ -445,11 +479,10 @@ __device__ __forceinline__ void deliver_cols(const DevNet &n, int t, int32_t *s_
                 if (x) red_add(&dst[loc], x);
             }
         }
-        if (threadIdx.x == 0) s_unit = gridDim.x + atomicAdd(&n.ctr->staged_cursor, 1u);
         __syncthreads();
-        col = s_unit;
+        col = s_unit[par];
     }
-    if (lane != 0) ev_all = ev_exc = 0;
+    if (lane != 0 && !n.tile) ev_all = ev_exc = 0;
     const unsigned long long ba = block_sum(ev_all);
     const unsigned long long be = block_sum(ev_exc);
     if (threadIdx.x == 0 && ba) {
@@ -458,7 +491,7 @@ __device__ __forceinline__ void deliver_cols(const DevNet &n, int t, int32_t *s_
     }
 }
 
-__global__ void __launch_bounds__(kStagedBlock) k_deliver_cols(DevNet n, const int *t_now)
+__device__ __forceinline__ void deliver_staged(const DevNet &n, const int *t_now, const Part &g)
 {
     extern __shared__ int4 smem_i4[];
     const int t = *t_now;
@@ -469,10 +502,10 @@ __global__ void __launch_bounds__(kStagedBlock) k_deliver_cols(DevNet n, const i
     uint32_t *s_hist = reinterpret_cast<uint32_t *>(s_in + kSlots * npc);   // [npc]
     int32_t *s_tile = reinterpret_cast<int32_t *>(s_hist + npc);         // [nwarps][kTileWords]
     uint16_t *s_x = reinterpret_cast<uint16_t *>(s_tile + nwarps * kTileWords);   // [kSlots * npc]
-    deliver_cols<true>(n, t, s_lut, s_in, s_tile, s_x, s_hist);
+    deliver_cols<true>(n, t, s_lut, s_in, s_tile, s_x, s_hist, g);
 }
 
-__global__ void __launch_bounds__(1024) k_deliver_ordered(DevNet n, const int *t_now)
+__device__ __forceinline__ void deliver_ordered(const DevNet &n, const int *t_now, const Part &g)
 {
     extern __shared__ int4 smem_i4[];
     const int t = *t_now;
@@ -483,7 +516,7 @@ __global__ void __launch_bounds__(1024) k_deliver_ordered(DevNet n, const int *t
     int32_t *s_ltd = s_in + npc;                                         // [npc]
     uint32_t *s_hist = reinterpret_cast<uint32_t *>(s_ltd + npc);        // [npc]
     int32_t *s_tile = reinterpret_cast<int32_t *>(s_hist + npc);         // [nwarps][kTileWords]
-    deliver_cols<false>(n, t, s_lut, s_in, s_tile, s_ltd, s_hist);
+    deliver_cols<false>(n, t, s_lut, s_in, s_tile, s_ltd, s_hist, g);
 }
 
 // ---------------------------------------------------------------------------
@@ -495,7 +528,7 @@ __global__ void __launch_bounds__(1024) k_deliver_ordered(DevNet n, const int *t
 // slot * npc + local id relative to the target's column, the delay and the
 // source row position; see rin32_entry) and 8 bytes otherwise.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_ltp(DevNet n, const int *t_now, int force)
+__device__ __forceinline__ void ltp_body(const DevNet &n, const int *t_now, int force, const Part &g)
 {
     __shared__ int32_t s_lut[kLut];
     __shared__ int32_t s_nb[32][kSlotStride];        // per warp: the neighbour columns of its target
@@ -510,7 +543,7 @@ __global__ void __launch_bounds__(1024) k_ltp(DevNet n, const int *t_now, int fo
     const int total = ce + ci;
     const int32_t *ring = n.ring_ids + (size_t)slot * n.N;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+    const uint32_t warps = part_threads(g) >> 5;
     const bool compact = n.rin32 != nullptr;
     int32_t *nb = s_nb[warp];
     auto spiker = [&](uint32_t item) -> int32_t {
@@ -520,7 +553,7 @@ __global__ void __launch_bounds__(1024) k_ltp(DevNet n, const int *t_now, int fo
     // item ahead, and the next one's entries go to L2 while this one is walked
     // (compact entries: lanes 0..15 hold the neighbour columns of those
     // spikers' columns, loaded as far ahead)
-    const uint32_t first = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t first = part_tid(g) >> 5;
     int64_t lo1 = 0, hi1 = 0, lo2 = 0, hi2 = 0;
     int32_t nb1 = 0, nb2 = 0;
     auto neighbours = [&](int32_t p) -> int32_t {
@@ -539,7 +572,8 @@ __global__ void __launch_bounds__(1024) k_ltp(DevNet n, const int *t_now, int fo
         nb2 = neighbours(p);
     }
     for (uint32_t item = first; item < (uint32_t)total; item += warps) {
-        const int64_t lo = lo1, hi = hi1;
+        int64_t lo = lo1, hi = hi1;
+        if (n.tile && !owned_column(n, (uint32_t)spiker(item) / n.npc)) hi = lo;   // another tile's synapses
         if (compact) {
             if (lane < kSlotStride) nb[lane] = nb1;
             __syncwarp();
@@ -608,7 +642,7 @@ __global__ void __launch_bounds__(1024) k_ltp(DevNet n, const int *t_now, int fo
 // fold the event-driven LTP accumulated in reverse order into the forward
 // derivatives (each forward excitatory synapse has exactly one reverse entry)
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_fold(DevNet n, const int *t_now, int force)
+__device__ __forceinline__ void fold_body(const DevNet &n, const int *t_now, int force, const Part &g)
 {
     if (!force) {
         const int t = *t_now;        // only before a long-term update (t closes a period)
@@ -624,7 +658,7 @@ __global__ void __launch_bounds__(1024) k_fold(DevNet n, const int *t_now, int f
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const bool compact = n.rin32 != nullptr;
     int32_t *nb = s_nb[warp];
-    for (uint32_t c0 = blockIdx.x * kFoldTargets; c0 < n.N;) {
+    for (uint32_t c0 = g.bid * kFoldTargets; c0 < n.N;) {
         const uint32_t c1 = min(c0 + kFoldTargets, n.N);
         for (uint32_t p = c0 + warp; p < c1; p += nw) {
             const int64_t lo = n.rin_off[p], hi = n.rin_off[p + 1];
@@ -668,7 +702,7 @@ __global__ void __launch_bounds__(1024) k_fold(DevNet n, const int *t_now, int f
             __syncwarp();
         }
         __syncthreads();
-        if (threadIdx.x == 0) s_chunk = (gridDim.x + atomicAdd(&n.ctr->fold_cursor, 1u)) * kFoldTargets;
+        if (threadIdx.x == 0) s_chunk = (g.nblk + atomicAdd(&n.ctr->fold_cursor, 1u)) * kFoldTargets;
         __syncthreads();
         c0 = s_chunk;
     }
@@ -679,7 +713,7 @@ __global__ void __launch_bounds__(1024) k_fold(DevNet n, const int *t_now, int f
 // excitatory row (grid-stride, so a step that closes no period costs one tiny
 // launch): w = clamp(w + bias + sd, 0, wmax), sd = (sd*decay + 2^15) >> 16.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_deriv(DevNet n, const int *t_now, int force)
+__device__ __forceinline__ void deriv_body(const DevNet &n, const int *t_now, int force, const Part &g)
 {
     const int t = *t_now;
     if (!n.deriv_period || t <= 0 || (t % (int)n.deriv_period) != 0) return;
@@ -687,8 +721,8 @@ __global__ void __launch_bounds__(1024) k_deriv(DevNet n, const int *t_now, int 
     if (!force && dense_selected(n, t)) return;
     const int lane = threadIdx.x & 31;
     const uint32_t rows = n.C * n.ne;
-    const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
-    for (uint32_t r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < rows; r += warps) {
+    const uint32_t warps = part_threads(g) >> 5;
+    for (uint32_t r = part_tid(g) >> 5; r < rows; r += warps) {
         const uint32_t p = (r / n.ne) * n.npc + (r % n.ne);
         const int64_t lo = row_base(n, p), hi = lo + row_len(n, p);
         for (int64_t k = lo + lane; k < hi; k += 32) {
@@ -777,14 +811,14 @@ template <> __device__ __forceinline__ float *state_u<float>(const DevNet &n) { 
 template <> __device__ __forceinline__ double *state_u<double>(const DevNet &n) { return n.ud; }
 
 template <typename F>
-__device__ __forceinline__ void neuron_body(const DevNet &n, const int *t_now, int *t_next)
+__device__ __forceinline__ void neuron_body(const DevNet &n, const int *t_now, int *t_next, const Part &g)
 {
     F *const sv = state_v<F>(n);
     F *const su = state_u<F>(n);
     const int t = *t_now;
     const int par = t & 1;
     const uint32_t tile = blockDim.x * kNeuronsPerThread;
-    const uint32_t first = blockIdx.x * tile;
+    const uint32_t first = g.bid * tile;
     uint32_t fe = 0, fi = 0;          // bit it: neuron first + it * blockDim + tid fired
     unsigned long long indeg = 0;     // excitatory in-degree of the neurons that fired
     // all loads of the thread's neurons first, then the updates and stores
@@ -807,10 +841,15 @@ __device__ __forceinline__ void neuron_body(const DevNet &n, const int *t_now, i
         if (i >= n.N) break;
         const bool exc = (i % n.npc) < n.ne;
         F v = vv[it], u = uu[it];
-        const bool fired = izhikevich_step(v, u, iq[it], exc);
+        // a tile leaves the neurons of other columns to their owners (their
+        // spikes of this step are injected afterwards)
+        const bool mine = !n.tile || owned_column(n, i / n.npc);
+        const bool fired = mine && izhikevich_step(v, u, iq[it], exc);
         n.I[i] = 0;
-        sv[i] = v;
-        su[i] = u;
+        if (mine) {
+            sv[i] = v;
+            su[i] = u;
+        }
         uint2 h = hh[it];
         if (h.x & 0x80000000u) h.y = (uint32_t)(t - 32);
         h.x = (h.x << 1) | (fired ? 1u : 0u);
@@ -874,7 +913,7 @@ __device__ __forceinline__ void neuron_body(const DevNet &n, const int *t_now, i
     if (threadIdx.x == 0) {
         if (bdeg) atomicAdd(&n.ctr->l_exc, bdeg);
         __threadfence();
-        s_last = atomicAdd(&n.ctr->done_blocks, 1u) == gridDim.x - 1;
+        s_last = atomicAdd(&n.ctr->done_blocks, 1u) == g.nblk - 1;
     }
     __syncthreads();
     if (!s_last || threadIdx.x != 0) return;
@@ -914,27 +953,166 @@ __device__ __forceinline__ void neuron_body(const DevNet &n, const int *t_now, i
 
 namespace snn {
 
+// membrane traces: v and u of the probed neurons after the update of step t
+__device__ __forceinline__ void probe_body(const DevNet &n, const int *t_now, const Part &g)
+{
+    const uint32_t k = part_tid(g);
+    if (k >= n.probe_n) return;
+    const int row = *t_now - n.probe_t0;
+    if (row < 0 || (uint32_t)row >= n.probe_cap) return;
+    const int32_t gid = n.probe_gid[k];
+    const size_t o = (size_t)row * n.probe_n + k;
+    n.probe_v[o] = n.vd ? (float)n.vd[gid] : n.v[gid];
+    n.probe_u[o] = n.ud ? (float)n.ud[gid] : n.u[gid];
+}
+
+
+// ---------------------------------------------------------------------------
+// kernels: one net over the whole grid, or every net of a batch in one
+// launch (each block works for the net its BatchLaunch table names, on that
+// net's own step, counters and cursors)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_deliver(DevNet n, const int *t_now) { deliver_ring(n, t_now, whole_grid()); }
+
+__global__ void __launch_bounds__(kStagedBlock) k_deliver_cols(DevNet n, const int *t_now)
+{
+    deliver_staged(n, t_now, whole_grid());
+}
+
+__global__ void __launch_bounds__(kOrderedMaxBlock, 5) k_deliver_ordered(DevNet n, const int *t_now)
+{
+    deliver_ordered(n, t_now, whole_grid());
+}
+
+__global__ void __launch_bounds__(1024) k_ltp(DevNet n, const int *t_now, int force)
+{
+    ltp_body(n, t_now, force, whole_grid());
+}
+
+__global__ void __launch_bounds__(1024) k_fold(DevNet n, const int *t_now, int force)
+{
+    fold_body(n, t_now, force, whole_grid());
+}
+
+__global__ void __launch_bounds__(1024) k_deriv(DevNet n, const int *t_now, int force)
+{
+    deriv_body(n, t_now, force, whole_grid());
+}
+
 __global__ void __launch_bounds__(1024) k_neuron_f32(DevNet n, const int *t_now, int *t_next)
 {
-    neuron_body<float>(n, t_now, t_next);
+    neuron_body<float>(n, t_now, t_next, whole_grid());
 }
 
 __global__ void __launch_bounds__(1024) k_neuron_f64(DevNet n, const int *t_now, int *t_next)
 {
-    neuron_body<double>(n, t_now, t_next);
+    neuron_body<double>(n, t_now, t_next, whole_grid());
 }
 
-// membrane traces: v and u of the probed neurons after the update of step t
-__global__ void k_probe(DevNet n, const int *t_now)
+__global__ void k_probe(DevNet n, const int *t_now) { probe_body(n, t_now, whole_grid()); }
+
+__global__ void __launch_bounds__(1024) k_deliver_b(BatchLaunch b)
 {
-    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n.probe_n) return;
-    const int row = *t_now - n.probe_t0;
-    if (row < 0 || (uint32_t)row >= n.probe_cap) return;
-    const int32_t g = n.probe_gid[k];
-    const size_t o = (size_t)row * n.probe_n + k;
-    n.probe_v[o] = n.vd ? (float)n.vd[g] : n.v[g];
-    n.probe_u[o] = n.ud ? (float)n.ud[g] : n.u[g];
+    const BatchBlock x = batch_block(b);
+    const DevNet n = b.nets[x.net];
+    deliver_ring(n, x.t_now, x.part);
+}
+
+__global__ void __launch_bounds__(kStagedBlock) k_deliver_cols_b(BatchLaunch b)
+{
+    const BatchBlock x = batch_block(b);
+    const DevNet n = b.nets[x.net];
+    deliver_staged(n, x.t_now, x.part);
+}
+
+__global__ void __launch_bounds__(kOrderedMaxBlock, 5) k_deliver_ordered_b(BatchLaunch b)
+{
+    const BatchBlock x = batch_block(b);
+    const DevNet n = b.nets[x.net];
+    deliver_ordered(n, x.t_now, x.part);
+}
+
+__global__ void __launch_bounds__(1024) k_ltp_b(BatchLaunch b)
+{
+    const BatchBlock x = batch_block(b);
+    const DevNet n = b.nets[x.net];
+    ltp_body(n, x.t_now, 0, x.part);
+}
+
+__global__ void __launch_bounds__(1024) k_fold_b(BatchLaunch b)
+{
+    const BatchBlock x = batch_block(b);
+    const DevNet n = b.nets[x.net];
+    fold_body(n, x.t_now, 0, x.part);
+}
+
+__global__ void __launch_bounds__(1024) k_deriv_b(BatchLaunch b)
+{
+    const BatchBlock x = batch_block(b);
+    const DevNet n = b.nets[x.net];
+    deriv_body(n, x.t_now, 0, x.part);
+}
+
+__global__ void __launch_bounds__(1024) k_neuron_f32_b(BatchLaunch b)
+{
+    const BatchBlock x = batch_block(b);
+    const DevNet n = b.nets[x.net];
+    neuron_body<float>(n, x.t_now, x.t_next, x.part);
+}
+
+__global__ void __launch_bounds__(1024) k_neuron_f64_b(BatchLaunch b)
+{
+    const BatchBlock x = batch_block(b);
+    const DevNet n = b.nets[x.net];
+    neuron_body<double>(n, x.t_now, x.t_next, x.part);
+}
+
+__global__ void k_probe_b(BatchLaunch b)
+{
+    const BatchBlock x = batch_block(b);
+    const DevNet n = b.nets[x.net];
+    probe_body(n, x.t_now, x.part);
+}
+
+// ---------------------------------------------------------------------------
+// a tile receives the spikes of step t of neurons it does not own (their
+// owners' compaction, Sec. 2 "Delivery of spiking messages"): each joins
+// ring slot t % D after the tile's own spikes of its kind, and its history
+// and last spike record it, so that delivery and potentiation see it as if
+// the neuron were the tile's own.  One thread per received spike; positions
+// come from the counts and a prefix within the launch (one block).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_inject(DevNet n, int t, const int32_t *gid, uint32_t count)
+{
+    __shared__ int s_base[2];
+    __shared__ uint32_t s_cnt[2];
+    const int slot = t % (int)n.D;
+    if (threadIdx.x == 0) {
+        s_base[0] = n.ring_cnt[2 * slot];
+        s_base[1] = n.ring_cnt[2 * slot + 1];
+        s_cnt[0] = s_cnt[1] = 0;
+    }
+    __syncthreads();
+    int32_t *ring = n.ring_ids + (size_t)slot * n.N;
+    for (uint32_t k0 = 0; k0 < count; k0 += blockDim.x) {
+        const uint32_t k = k0 + threadIdx.x;
+        if (k < count) {
+            const uint32_t g = (uint32_t)gid[k];
+            if (!out_of_range(n, g < n.N)) {
+                const bool exc = (g % n.npc) < n.ne;
+                const uint32_t pos = atomicAdd(&s_cnt[exc ? 0 : 1], 1u);
+                const int at = exc ? s_base[0] + (int)pos : (int)n.N - 1 - (s_base[1] + (int)pos);
+                if (!out_of_range(n, at >= 0 && at < (int)n.N)) ring[at] = (int32_t)g;
+                n.hl[g].x |= 1u;                 // bit 0: fired at t (the step's update has run)
+                n.last_spike[g] = t;
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        n.ring_cnt[2 * slot] = s_base[0] + (int)s_cnt[0];
+        n.ring_cnt[2 * slot + 1] = s_base[1] + (int)s_cnt[1];
+    }
 }
 
 }  // namespace snn

@@ -126,9 +126,14 @@ _SIGS = {
     "snn_batch_create": (ctypes.c_int, [_vp, ctypes.c_uint32, ctypes.c_uint32, _P(_vp)]),
     "snn_batch_run": (ctypes.c_int, [_vp, ctypes.c_uint32]),
     "snn_batch_free": (None, [_vp]),
+    "snn_batch_set_launch": (ctypes.c_int, [_vp, _P(SnnLaunch)]),
+    "snn_batch_get_launch": (ctypes.c_int, [_vp, _P(SnnLaunch)]),
+    "snn_batch_autotune": (ctypes.c_int, [_vp, ctypes.c_uint32, _P(SnnLaunch)]),
     "snn_thalamic_events": (ctypes.c_int, [_P(SnnConfig), ctypes.c_int32, ctypes.c_uint32, _vp, ctypes.c_size_t,
                                            _P(ctypes.c_size_t)]),
     "snn_microbench_atomics": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_uint32, _vp, _P(SnnAtomicRates)]),
+    "snn_set_tile": (ctypes.c_int, [_vp, ctypes.c_uint32, ctypes.c_uint32]),
+    "snn_inject_spikes": (ctypes.c_int, [_vp, _vp, ctypes.c_uint32]),
     "snn_free": (None, [_vp]),
     "snn_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "snn_last_error": (ctypes.c_char_p, []),
@@ -382,6 +387,15 @@ class Network:
         out = out[: n.value]
         return out["t"].copy(), out["gid"].copy()
 
+    def set_tile(self, first_col: int, n_cols: int):
+        """Own (integrate, deliver to) columns [first_col, first_col + n_cols) only."""
+        _check(self._lib.snn_set_tile(self.h, int(first_col), int(n_cols)), "snn_set_tile")
+
+    def inject_spikes(self, gids):
+        """Spikes of the last step of neurons owned by other tiles."""
+        g = np.ascontiguousarray(gids, np.int32)
+        _check(self._lib.snn_inject_spikes(self.h, _ptr(g) if len(g) else None, len(g)), "snn_inject_spikes")
+
     def set_thalamic(self, on: bool):
         _check(self._lib.snn_set_thalamic(self.h, int(bool(on))), "snn_set_thalamic")
 
@@ -509,8 +523,9 @@ class Network:
 
 
 class Batch:
-    """Many independent nets advanced together by one CUDA graph per chunk of
-    steps (each net a parallel branch).  Does not own the nets."""
+    """Many independent nets advanced together: one CUDA graph per chunk of
+    steps, one launch per kind of step kernel per step for all nets.  Does
+    not own the nets."""
 
     def __init__(self, nets, graph_steps: int = 10):
         self._lib = load()
@@ -522,6 +537,23 @@ class Batch:
 
     def run(self, n_ms: int):
         _check(self._lib.snn_batch_run(self.h, int(n_ms)), "snn_batch_run")
+
+    def set_launch(self, **fields):
+        L = SnnLaunch()
+        for k, v in fields.items():
+            setattr(L, k, int(v))
+        _check(self._lib.snn_batch_set_launch(self.h, ctypes.byref(L)), "snn_batch_set_launch")
+
+    def get_launch(self) -> dict:
+        L = SnnLaunch()
+        _check(self._lib.snn_batch_get_launch(self.h, ctypes.byref(L)), "snn_batch_get_launch")
+        return {k: getattr(L, k) for k, _ in SnnLaunch._fields_}
+
+    def autotune(self, probe_ms: int = 50) -> dict:
+        """Pick the fastest batch launch shape; every net is left reset at t = 0."""
+        L = SnnLaunch()
+        _check(self._lib.snn_batch_autotune(self.h, int(probe_ms), ctypes.byref(L)), "snn_batch_autotune")
+        return {k: getattr(L, k) for k, _ in SnnLaunch._fields_}
 
     def close(self):
         if getattr(self, "h", None) is not None and self.h.value:

@@ -135,7 +135,7 @@ def test_compact_target_slot_decode_is_exact():
 
 
 def test_readme_c_example_builds_and_fails_loudly_without_a_gpu(tmp_path):
-    # the README's plain-C program compiles warning-free against the header
+    # the example C program compiles warning-free against the header
     # and links against the library; on a machine without a GPU the first
     # call reports a CUDA error and the program exits 1 (there is no CPU path)
     import torch
@@ -148,11 +148,10 @@ def test_readme_c_example_builds_and_fails_loudly_without_a_gpu(tmp_path):
 
 
 def test_readme_c_example_configures_the_one_column_workload():
-    # every "c.field = value;" of the README program, evaluated, equals the
+    # every "c.field = value;" of the example program, evaluated, equals the
     # col1_m100 workload (the GPU test compares the program's output with the
     # oracle on that workload)
-    text = open(os.path.join(ROOT, "README.md")).read()
-    code = re.search(r"```c\n(.*?)```", text, re.S).group(1)
+    code = open(os.path.join(ROOT, "examples", "readme_example.c")).read()
     got = {}
     for field, idx, expr in re.findall(r"\bc\.(\w+)(?:\[(\d)\])?\s*=\s*([^;]+);", code):
         value = eval(expr, {})

@@ -51,7 +51,8 @@ def test_clock_samples_are_summarised(tmp_path):
     s = bench.ClockSampler.__new__(bench.ClockSampler)
     s.path = str(path)
     s.f = open(os.devnull, "w")
-    s.proc = types.SimpleNamespace(terminate=lambda: None, wait=lambda timeout=None: 0, kill=lambda: None)
+    s.proc = types.SimpleNamespace(terminate=lambda: None, wait=lambda timeout=None: 0, kill=lambda: None,
+                                   poll=lambda: 0)
     out = s.stop()
     assert out == {"sm_mhz": 1980.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
     assert not path.exists()
@@ -141,6 +142,8 @@ def test_serving_leg_reports_latency_and_throughput(monkeypatch):
     assert set(leg["latency"]) == {"p50_s", "p99_s", "mean_s", "max_s"}
     assert leg["latency"]["p50_s"] <= leg["latency"]["p99_s"] <= leg["latency"]["max_s"]
     assert leg["sim_ms_total"] >= 6 * 100 and not ts.FakeNet.live
+    # the same requests one at a time: same events, and the ratio reported
+    assert leg["one_at_a_time"]["same_events"] and leg["speedup"] > 0
 
 
 class _FakeBenchNet:
@@ -244,7 +247,8 @@ def test_main_line_carries_every_key_with_a_fake_engine(monkeypatch, capsys):
                         lambda nbytes, ops, stream=None: {"red_global_window_gops": 200.0,
                                                           "atom_shared_window_gops": 2000.0})
     monkeypatch.setattr(bench, "dist_env", lambda: (0, 0, 1))
-    monkeypatch.setattr(sys, "argv", ["bench.py", "--steps", "5", "--warmup", "3", "--serve-requests", "4"])
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--steps", "5", "--warmup", "3", "--serve-requests", "4",
+                                      "--batch-nets", "0"])
     assert bench.main() == 0
     lines = [ln for ln in capsys.readouterr().out.splitlines() if ln.startswith("{")]
     assert len(lines) == 1

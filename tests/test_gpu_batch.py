@@ -143,3 +143,87 @@ def test_autotune_keeps_results(eng):
         assert n.counters()["t"] == 0 and shape["graph_steps"] in (10, 50)
         n.run(1010)
         _same(_state(n), r)
+
+
+def test_batch_autotune_and_shapes_keep_results(eng):
+    # the batch's own launch shapes (threads per column, resident blocks,
+    # chunk length) and its autotuner change nothing in the results
+    cfgs = _small_mix()[:4]
+    T = 1010
+    alone = []
+    for c in cfgs:
+        with _net(eng, c, T) as n:
+            n.run(T)
+            alone.append(_state(n))
+    nets = [_net(eng, c, T) for c in cfgs]
+    try:
+        with eng.Batch(nets, graph_steps=10) as b:
+            b.set_launch(deliver_block=64, deliver_blocks_per_sm=1, ltp_blocks_per_sm=1, neuron_block=32,
+                         graph_steps=4)
+            assert b.get_launch()["graph_steps"] == 4
+            b.run(T)
+            for n, ref in zip(nets, alone):
+                _same(_state(n), ref)
+            shape = b.autotune(probe_ms=20)
+            assert shape["deliver_block"] in (128, 256) and shape["graph_steps"] in (10, 50)
+            assert all(n.counters()["t"] == 0 for n in nets)
+            b.run(T)
+        for n, ref in zip(nets, alone):
+            _same(_state(n), ref)
+    finally:
+        for n in nets:
+            n.close()
+
+
+def _digest_state(n, T):
+    import hashlib
+    h = hashlib.sha256()
+    t, g = n.raster(0, T)
+    h.update(np.stack([t, g], axis=1).astype("<i4").tobytes())
+    nn = n.neurons()
+    h.update(nn["v"].view(np.int32).tobytes())
+    h.update(nn["u"].view(np.int32).tobytes())
+    c = n.counters()
+    h.update(np.array([c["spikes"], c["e_all"], c["e_exc"], c["l_exc"]], np.int64).tobytes())
+    # the synapses of the first and last source rows (weights and derivatives)
+    for p in (0, workloads.n_neurons(n.cfg) - 1):
+        syn = n.synapses(p, 1)
+        h.update(syn["w"].astype("<i4").tobytes())
+        h.update(syn["sd"].astype("<i4").tobytes())
+    return h.hexdigest()
+
+
+def test_batch_of_256_uneven_nets_equals_nets_run_alone(eng):
+    # the batched workload's 256 nets (grid side 1..16, M in {100, 400,
+    # 1125}, seeds 1000..1255) in waves that fit the device: every net's
+    # raster, neuron state, counters and sampled synapses after 30 steps are
+    # identical batched and alone
+    import torch
+    cfgs = workloads.batch_workloads()
+    assert len(cfgs) == 256
+    T = 30
+    budget = int(min(100e9, 0.6 * torch.cuda.mem_get_info()[0]))
+    i = 0
+    while i < len(cfgs):
+        wave, used = [], 0
+        while i < len(cfgs):
+            n = eng.Network(cfgs[i], raster_capacity=workloads.n_neurons(cfgs[i]) * T + 1024)
+            if wave and used + n.device_bytes > budget:
+                n.close()
+                break
+            wave.append(n)
+            used += n.device_bytes
+            i += 1
+        try:
+            alone = []
+            for n in wave:
+                n.run(T)
+                alone.append(_digest_state(n, T))
+                n.reset()
+            with eng.Batch(wave, graph_steps=10) as b:
+                b.run(T)
+            for n, ref in zip(wave, alone):
+                assert _digest_state(n, T) == ref, n.cfg["name"]
+        finally:
+            for n in wave:
+                n.close()

@@ -1,6 +1,6 @@
 """Continuous batching: requests admitted while others run, memory freed as
 they finish; every request's raster and weights must be identical to the
-same request run alone."""
+same request run alone, and to the oracle's run of that request."""
 import numpy as np
 import pytest
 
@@ -9,7 +9,7 @@ import workloads
 pytestmark = pytest.mark.gpu
 
 
-def test_served_results_equal_alone():
+def test_served_results_equal_alone(orc):
     import paper_1310_8478_gb300 as eng
     from paper_1310_8478_gb300 import serve, snn
     eng.build_engine()
@@ -39,5 +39,14 @@ def test_served_results_equal_alone():
     for r in res:
         assert (r.raster_digest, r.weights_digest, r.events) == alone[r.rid], r.rid
         assert r.done_s >= r.admitted_s >= r.arrival_s - 1e-9
+    # and to the oracle, request by request
+    for r in reqs:
+        o = orc.Oracle(r.cfg)
+        o.run(r.duration_ms)
+        ot, og = o.raster()
+        syn = o.synapses()
+        assert serve.digest(ot, og) == alone[r.rid][0], r.rid
+        assert serve.digest(syn["w"], syn["sd"]) == alone[r.rid][1], r.rid
+        assert o.counters()["e_all"] == alone[r.rid][2], r.rid
     stats = serve.latency_stats(res)
     assert stats["p99_s"] >= stats["p50_s"] > 0

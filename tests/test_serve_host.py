@@ -36,6 +36,9 @@ class FakeNet:
     def counters(self):
         return {"t": self.t, "spikes": self.t * 2, "e_all": self.t * self.n}
 
+    def run(self, n_ms):
+        self.t += n_ms
+
     def raster(self):
         return np.arange(self.t), np.zeros(self.t)
 

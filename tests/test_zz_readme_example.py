@@ -1,4 +1,4 @@
-"""The plain-C program of README.md, run on the GPU: what it prints (spike and
+"""The plain-C example program (examples/readme_example.c), run on the GPU: what it prints (spike and
 event counts of one simulated second, first spike of the raster) equals the
 oracle's figures for the same one-column workload.  Collected after the other
 GPU tests, so that a stop at the first failure has run everything else."""
@@ -17,7 +17,7 @@ def test_readme_c_example_matches_the_oracle(tmp_path, orc):
     exe = build_readme_c_example(tmp_path, e.build_engine())
     r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stderr
-    # the README's configuration is the one-column benchmark workload
+    # the example's configuration is the one-column benchmark workload
     o = orc.Oracle(workloads.workload("col1_m100"))
     o.run(1000)
     c = o.counters()
