@@ -284,6 +284,11 @@ def batch_leg(n_nets: int, steps: int, budget_gb: float, stream, autotune_ms: in
     shape = None
     ev_a = torch.cuda.Event(enable_timing=True)
     ev_b = torch.cuda.Event(enable_timing=True)
+    by_kind = {}
+
+    def kind_of(c):
+        side = "side 1-4" if c["grid_x"] <= 4 else ("side 5-10" if c["grid_x"] <= 10 else "side 11-16")
+        return "M=%d, %s" % (c["fanout"], side)
 
     def timed(fn):
         torch.cuda.synchronize()
@@ -310,11 +315,22 @@ def batch_leg(n_nets: int, steps: int, budget_gb: float, stream, autotune_ms: in
             n.run(warm)
         e0 = sum(n.counters()["e_all"] for n in wave)
 
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in wave]
+        c_before = [n.counters()["e_all"] for n in wave]
+
         def alone():
-            for n in wave:
+            for n, (a, b) in zip(wave, evs):
+                a.record(stream)
                 n.run(steps)
+                b.record(stream)
         seq_ms += timed(alone)
         seq_ev += sum(n.counters()["e_all"] for n in wave) - e0
+        for n, (a, b), c0 in zip(wave, evs, c_before):
+            kind = kind_of(n.cfg)
+            k = by_kind.setdefault(kind, {"nets": 0, "one_at_a_time_ms": 0.0, "events": 0})
+            k["nets"] += 1
+            k["one_at_a_time_ms"] += a.elapsed_time(b)
+            k["events"] += n.counters()["e_all"] - c0
         ref = [raster_digest(n, 0, T) for n in wave]
         for n in wave:
             n.reset()
@@ -339,7 +355,13 @@ def batch_leg(n_nets: int, steps: int, budget_gb: float, stream, autotune_ms: in
            "value": bat_ev / (bat_ms / 1e3), "batched_ms": round(bat_ms, 3),
            "one_at_a_time": seq_ev / (seq_ms / 1e3), "one_at_a_time_ms": round(seq_ms, 3),
            "speedup": (bat_ev / bat_ms) / (seq_ev / seq_ms), "same_events": seq_ev == bat_ev,
-           "raster_digests_equal": same, "events": bat_ev}
+           "raster_digests_equal": same, "events": bat_ev,
+           # where the one-at-a-time time goes: batching can only take away
+           # the launch-bound share of the small nets
+           "one_at_a_time_by_kind": {k: {"nets": v["nets"], "ms": round(v["one_at_a_time_ms"], 3),
+                                         "share": round(v["one_at_a_time_ms"] / max(seq_ms, 1e-9), 4),
+                                         "events_per_s": v["events"] / max(v["one_at_a_time_ms"] / 1e3, 1e-12)}
+                                     for k, v in sorted(by_kind.items())}}
     if shape is not None:
         out["autotuned"] = {k: shape[k] for k in ("deliver_block", "deliver_blocks_per_sm", "graph_steps")}
     return out

@@ -136,6 +136,13 @@ typedef struct {
                                         many per 1000 neurons; 0xffffffff = never (the default:
                                         the column-ordered delivery, which stages the source
                                         column's own neurons, is faster on the measured nets) */
+    uint32_t ring_permille;          /* nets with compact targets: a step without the dense pass
+                                        whose expected events stay below this many per 1000
+                                        neurons delivers from the ring's spike lists instead of
+                                        walking every column (default: never, i.e. 0, which a
+                                        shape cannot set again since 0 means "unchanged": 1 is
+                                        practically never; 0xffffffff = every such step).  Off by
+                                        default: slower than the column walk on the measured nets */
 } snn_launch;
 
 /* Per-kernel device time collected while profiling is on (CUDA events), and

@@ -459,6 +459,7 @@ int setup_dense(snn_net *net)
     net->dn.staged_ok = 0;
     net->dn.staged_min_events = ~0ull;
     net->dn.ordered_ok = 0;
+    net->dn.ring_max_events = 0;
     if (!net->tgt16) return SNN_OK;
     {
         // the column-ordered delivery: deliver_block threads per column, at
@@ -472,6 +473,8 @@ int setup_dense(snn_net *net)
         if (per_sm >= 1) {
             net->dn.ordered_ok = 1;
             net->ordered_grid = (int)std::min<int64_t>(net->dn.C, (int64_t)per_sm * net->sm_count);
+            const uint32_t pm = net->launch.ring_permille;
+            net->dn.ring_max_events = pm == 0xffffffffu ? ~0ull : (unsigned long long)net->N * pm / 1000ull;
         }
     }
     // a tile takes the column-ordered delivery in every step (it alone
@@ -635,6 +638,11 @@ int start_net(const snn_config *cfg, void *cuda_stream, size_t budget, snn_net *
     // 64x64 M = 1125 onset and the 128x128 paper geometry): off by default
     // (no launch); a launch shape can still ask for it
     net->launch.staged_permille = 0xffffffffu;
+    // the ring-list delivery for steps with few events is off by default:
+    // on the 64x64 onset it took 0.64 ms at 1-2 M events (its global
+    // reductions into the source's own column contend) against 0.07 ms for
+    // the column walk
+    net->launch.ring_permille = 0;
     (void)cuda_stream;
     return SNN_OK;
 }
@@ -737,11 +745,15 @@ void launch_step(snn_net *net, int32_t t, cudaStream_t s, bool exact_t)
         mark(3);
     }
     mark(0);
-    if (dn.ordered_ok)
+    if (dn.ordered_ok) {
         k_deliver_ordered<<<net->ordered_grid, ordered_block(L.deliver_block),
                             ordered_smem_bytes(dn.npc, ordered_block(L.deliver_block)), s>>>(dn, t_now);
-    else k_deliver<<<g_del, L.deliver_block, 0, s>>>(dn, t_now);
-    ++launched;
+        ++launched;
+    }
+    if (!dn.ordered_ok || dn.ring_max_events) {
+        k_deliver<<<g_del, L.deliver_block, 0, s>>>(dn, t_now);
+        ++launched;
+    }
     if (dn.staged_ok) {
         k_deliver_cols<<<net->staged_grid, kStagedBlock, staged_smem_bytes(dn.npc, kStagedBlock), s>>>(dn, t_now);
         ++launched;
@@ -1261,6 +1273,7 @@ int snn_set_launch(snn_net *net, const snn_launch *launch)
     L.dense_rows = pick(launch->dense_rows, L.dense_rows);
     L.dense_permille = pick(launch->dense_permille, L.dense_permille);
     L.staged_permille = pick(launch->staged_permille, L.staged_permille);
+    L.ring_permille = pick(launch->ring_permille, L.ring_permille);
     for (uint32_t b : {L.deliver_block, L.neuron_block, L.ltp_block, L.deriv_block}) {
         if (b < 32 || b > 1024 || b % 32) { set_error("block sizes must be multiples of 32 in 32..1024"); return SNN_EINVAL; }
     }
@@ -1481,7 +1494,7 @@ int batch_tables(snn_batch *b)
                                                L.deliver_blocks_per_sm), cnt[kBOrdered]);
     for (size_t i = 0; i < nn; ++i) {
         const snn_net *n = b->nets[i];
-        w[i] = n->dn.ordered_ok ? 0.0 : work(i);
+        w[i] = (!n->dn.ordered_ok || n->dn.ring_max_events) ? work(i) : 0.0;
         cap[i] = ((uint64_t)n->N * n->dn.D / 4 + L.deliver_block - 1) / L.deliver_block;
     }
     b->kind[kBRing].block = L.deliver_block;

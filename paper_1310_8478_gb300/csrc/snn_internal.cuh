@@ -40,6 +40,8 @@ struct DevCounters {
     unsigned dense_cursor;           // work units of the dense pass handed out in this step
     unsigned staged_cursor;          // columns of the column-staged delivery handed out in this step
     unsigned fold_cursor;            // chunks of reverse entries handed out by the current fold
+    int sd_rev_dirty;                // the event-driven potentiation wrote sd_rev since the last fold
+    unsigned fold_done;              // blocks of the current fold finished (the last one clears the flag)
 };
 
 // Everything a step kernel needs, passed by value.
@@ -49,6 +51,8 @@ struct DevNet {
     int staged_ok;                   // the column-staged delivery may run (compact targets, staging fits)
     int ordered_ok;                  // the column-ordered delivery replaces the ring-order one (compact targets)
     unsigned long long staged_min_events;   // it runs when a step's expected events reach this
+    unsigned long long ring_max_events;     // compact nets: a step whose expected events stay below this
+                                            // delivers from the ring's spike lists (0: never)
     int32_t w_inh;                   // generated nets: the weight of every inhibitory synapse (not
                                      //                 plastic); the dense pass reads no inhibitory w
     uint32_t uniform_m;              // > 0: row p starts at p * uniform_m (generated nets; the
@@ -306,25 +310,45 @@ __device__ __forceinline__ bool out_of_range(const DevNet &, bool)
 }
 #endif
 
-// a step without the dense pass delivers column by column through shared
-// memory when its expected events reach staged_min_events: excitatory spikes
-// of t - d reach bucket d (about M / D synapses), inhibitory spikes of t - 1
-// their whole row (generated nets: inhibitory delay 1)
-__device__ __forceinline__ bool staged_selected(const DevNet &n, int t)
+// a step's expected events: excitatory spikes of t - d reach bucket d (about
+// M / D synapses), inhibitory spikes of t - 1 their whole row (generated
+// nets: inhibitory delay 1)
+__device__ __forceinline__ unsigned long long expected_events(const DevNet &n, int t)
 {
-    if (!n.staged_ok || t < 1 || dense_selected(n, t)) return false;
+    if (t < 1) return 0;
     unsigned long long exc = 0;
     for (int d = 1; d <= (int)n.D && d <= t; ++d) exc += (unsigned)n.ring_cnt[2 * ((t - d) % (int)n.D)];
     const unsigned long long inh = (unsigned)n.ring_cnt[2 * ((t - 1) % (int)n.D) + 1];
-    const unsigned long long est = exc * n.canon_m / n.D + inh * n.canon_m;
-    return est >= n.staged_min_events;
+    return exc * n.canon_m / n.D + inh * n.canon_m;
 }
 
-// compact nets deliver the remaining event-driven steps column by column with
-// global reductions
+// a step without the dense pass delivers column by column through shared
+// memory when its expected events reach staged_min_events
+__device__ __forceinline__ bool staged_selected(const DevNet &n, int t)
+{
+    if (!n.staged_ok || t < 1 || dense_selected(n, t)) return false;
+    return expected_events(n, t) >= n.staged_min_events;
+}
+
+// compact nets deliver a step with few expected events from the ring's
+// spike lists (a few rounds of latency, no scan of every row's history)
+__device__ __forceinline__ bool light_selected(const DevNet &n, int t)
+{
+    return n.ordered_ok && !n.tile && n.ring_max_events && !dense_selected(n, t) && !staged_selected(n, t) &&
+           expected_events(n, t) < n.ring_max_events;
+}
+
+// compact nets deliver the remaining event-driven steps column by column
 __device__ __forceinline__ bool ordered_selected(const DevNet &n, int t)
 {
-    return n.ordered_ok && !dense_selected(n, t) && !staged_selected(n, t);
+    return n.ordered_ok && !dense_selected(n, t) && !staged_selected(n, t) && !light_selected(n, t);
+}
+
+// the ring-order delivery: nets without compact targets, and light steps
+__device__ __forceinline__ bool ring_selected(const DevNet &n, int t)
+{
+    if (dense_selected(n, t) || staged_selected(n, t)) return false;
+    return !n.ordered_ok || light_selected(n, t);
 }
 
 __device__ __forceinline__ int64_t row_base(const DevNet &n, uint32_t p)

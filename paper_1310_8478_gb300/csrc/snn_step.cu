@@ -51,7 +51,7 @@ __device__ __forceinline__ void deliver_ring(const DevNet &n, const int *t_now, 
     __shared__ int s_tile_start[32 * 33];        // per warp: prefix of the items' lengths
     __shared__ uint32_t s_tile_info[32 * 32];    // per warp: kind and source column of each item
     const int t = *t_now;
-    if (dense_selected(n, t) || staged_selected(n, t) || n.ordered_ok) return;
+    if (!ring_selected(n, t)) return;
     const bool stdp = !(n.flags & SNN_STDP_OFF);
     const int nl = (int)(n.D + n.D_inh);
     for (int i = threadIdx.x; i < kLut; i += blockDim.x) s_lut[i] = n.lut_m[i];
@@ -211,7 +211,7 @@ size_t staged_smem_bytes(uint32_t npc, uint32_t block)
 
 size_t ordered_smem_bytes(uint32_t npc, uint32_t block)
 {
-    return (size_t)kLut * 4 + (size_t)npc * 12 + (size_t)(block / 32) * kTileWords * 4;
+    return (size_t)kLut * 4 + (size_t)npc * 16 + (size_t)(block / 32) * kTileWords * 4;
 }
 
 // s_amt: kStage -> uint16 LTD amounts of the 13 staged columns;
@@ -219,11 +219,12 @@ size_t ordered_smem_bytes(uint32_t npc, uint32_t block)
 // s_hist: the history words (bit k: fired at t - k) of the column's rows.
 template <bool kStage>
 __device__ __forceinline__ void deliver_cols(const DevNet &n, int t, int32_t *s_lut, int32_t *s_in, int32_t *s_tile,
-                                             void *s_amt, uint32_t *s_hist, const Part &g)
+                                             void *s_amt, uint32_t *s_hist, const Part &g, uint32_t *s_inh = nullptr)
 {
     __shared__ uint32_t s_col[kSlots];
     __shared__ uint32_t s_unit[2];             // the next column, claimed while this one is walked
     __shared__ uint32_t s_grp;                 // row groups of the current column handed out
+    __shared__ uint32_t s_ninh;                // inhibitory rows of the column that fired at t - 1
     uint16_t *s_x = reinterpret_cast<uint16_t *>(s_amt);
     int32_t *s_ltd = reinterpret_cast<int32_t *>(s_amt);
     const uint32_t npc = n.npc;
@@ -233,6 +234,7 @@ __device__ __forceinline__ void deliver_cols(const DevNet &n, int t, int32_t *s_
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < kLut; i += blockDim.x) s_lut[i] = n.lut_m[i];
     drive(n, t, part_tid(g), part_threads(g));
+    __syncthreads();                  // the table is read by every thread's column setup below
     const int D = (int)n.D;
     const uint32_t dmask_e = (2u << D) - 2u, dmask_i = (2u << n.D_inh) - 2u;
     int32_t *w_c0 = s_tile + warp * kTileWords;                // [32] first chunk (column-relative)
@@ -247,6 +249,7 @@ __device__ __forceinline__ void deliver_cols(const DevNet &n, int t, int32_t *s_
         if (threadIdx.x < kSlots) s_col[threadIdx.x] = (uint32_t)n.nbr[col * kSlotStride + threadIdx.x];
         if (threadIdx.x == 0) {
             s_grp = 0;
+            s_ninh = 0;
             s_unit[par] = g.nblk + atomicAdd(&n.ctr->staged_cursor, 1u);
         }
         if (kStage) __syncthreads();
@@ -402,10 +405,42 @@ __device__ __forceinline__ void deliver_cols(const DevNet &n, int t, int32_t *s_
             }
             __syncwarp();
         };
+        // Without 13-column staging, the inhibitory rows that fired at t - 1
+        // are walked by the whole block first: such a row delivers all of its
+        // synapses at delay 1, with one weight, to excitatory neurons of its
+        // own column (generated nets), so the block lists them and spreads
+        // the concatenated rows' chunks over all threads -- an even share
+        // whatever the rows' distribution over the groups.
+        if (!kStage) {
+            const bool mine = deliver_on && (!n.tile || owned_column(n, col));
+            if (mine)
+                for (uint32_t r = n.ne + threadIdx.x; r < npc; r += blockDim.x)
+                    if (s_hist[r] & 1u) s_inh[atomicAdd(&s_ninh, 1u)] = r;
+            __syncthreads();
+            const uint32_t ninh = s_ninh;
+            const uint32_t m = n.canon_m, cpr = (m + 7u) / 8u;
+            for (uint32_t c = threadIdx.x; c < ninh * cpr; c += blockDim.x) {
+                const uint32_t it = c / cpr, ci = c - it * cpr;
+                const int64_t k0 = (int64_t)s_inh[it] * n.uniform_m + 8 * ci;   // column-relative
+                if (out_of_range(n, k0 + 8 <= col_syn && cbase + k0 + 8 <= n.S)) continue;
+                const uint4 tv = t4[k0 >> 3];
+                const uint32_t nv = min(8u, m - 8u * ci);
+                const uint32_t tw[4] = {tv.x, tv.y, tv.z, tv.w};
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const uint32_t v = (tw[u >> 1] >> (16 * (u & 1))) & 0xffffu;
+                    if ((uint32_t)u < nv && !out_of_range(n, v < npc)) atomicAdd(&s_in[v], n.w_inh);
+                }
+            }
+            if (threadIdx.x == 0) ev_all += (unsigned long long)ninh * m;
+        }
         // Items (row << 5 | bucket) collect in the warp's buffer across row
         // groups and are walked 32 at a time, so that a tile is full even when
         // few rows of a group fired; a group with too many items for the
         // buffer is walked directly, one flagged bucket per lane and pass.
+        // (Without staging the inhibitory rows are done above: the groups
+        // cover the excitatory rows only.)
+        const uint32_t ngroups_w = kStage ? ngroups : (n.ne + 31u) / 32u;
         int cnt = 0;                                   // items in the buffer
         bool groups_left = true;                       // warp-uniform
         uint32_t fb = 0, r = 0;                        // a group walked directly: its remaining flags
@@ -430,13 +465,13 @@ __device__ __forceinline__ void deliver_cols(const DevNet &n, int t, int32_t *s_
                 uint32_t grp = 0;
                 if (lane == 0) grp = atomicAdd(&s_grp, 1u);
                 grp = __shfl_sync(0xffffffffu, grp, 0);
-                if (grp >= ngroups) {
+                if (grp >= ngroups_w) {
                     groups_left = false;
                     continue;
                 }
-                r = (ngroups - 1u - grp) * 32u + lane;   // the last groups (inhibitory rows) first
+                r = (ngroups_w - 1u - grp) * 32u + lane;   // the last groups (inhibitory rows) first
                 uint32_t f = 0;                        // bit d: the row's source fired at t - d
-                if (r < npc) f = (s_hist[r] << 1) & (r < n.ne ? dmask_e : dmask_i);
+                if (r < npc && (kStage || r < n.ne)) f = (s_hist[r] << 1) & (r < n.ne ? dmask_e : dmask_i);
                 const int mine = __popc(f);
                 int incl = mine;
 #pragma unroll
@@ -445,7 +480,11 @@ __device__ __forceinline__ void deliver_cols(const DevNet &n, int t, int32_t *s_
                     if (lane >= o) incl += y;
                 }
                 const int total = __shfl_sync(0xffffffffu, incl, 31);
-                if (cnt + total <= kItemCap) {
+                // a group of inhibitory rows is walked at once: each of its
+                // items is a whole row, long enough to fill a tile, and
+                // walking them first is what the longest-first order is for
+                const bool inh_group = (r - lane) >= n.ne;
+                if (!inh_group && cnt + total <= kItemCap) {
                     int pos = cnt + incl - mine;
                     while (f) {
                         w_items[pos++] = (r << 5) | (uint32_t)(__ffs(f) - 1);
@@ -454,7 +493,7 @@ __device__ __forceinline__ void deliver_cols(const DevNet &n, int t, int32_t *s_
                     cnt += total;
                     __syncwarp();
                 } else {
-                    fb = f;                            // too many for the buffer: walk this group directly
+                    fb = f;                            // walk this group directly, one flagged bucket per lane and pass
                 }
                 continue;
             } else {
@@ -515,8 +554,9 @@ __device__ __forceinline__ void deliver_ordered(const DevNet &n, const int *t_no
     int32_t *s_in = s_lut + kLut;                                        // [npc]
     int32_t *s_ltd = s_in + npc;                                         // [npc]
     uint32_t *s_hist = reinterpret_cast<uint32_t *>(s_ltd + npc);        // [npc]
-    int32_t *s_tile = reinterpret_cast<int32_t *>(s_hist + npc);         // [nwarps][kTileWords]
-    deliver_cols<false>(n, t, s_lut, s_in, s_tile, s_ltd, s_hist, g);
+    uint32_t *s_inh = s_hist + npc;                                      // [npc]
+    int32_t *s_tile = reinterpret_cast<int32_t *>(s_inh + npc);          // [nwarps][kTileWords]
+    deliver_cols<false>(n, t, s_lut, s_in, s_tile, s_ltd, s_hist, g, s_inh);
 }
 
 // ---------------------------------------------------------------------------
@@ -536,16 +576,20 @@ __device__ __forceinline__ void ltp_body(const DevNet &n, const int *t_now, int 
     const int tp = t - 1;
     if (n.ctr->ltp_pending != tp || (n.flags & SNN_STDP_OFF)) return;
     if (!force && dense_selected(n, t)) return;
-    for (int i = threadIdx.x; i < kLut; i += blockDim.x) s_lut[i] = n.lut_p[i];
-    __syncthreads();
     const int slot = tp % (int)n.D;
     const int ce = n.ring_cnt[2 * slot], ci = n.ring_cnt[2 * slot + 1];
     const int total = ce + ci;
+    // a block whose first warp has no spiker leaves at once (steps with few
+    // spikes use a small part of the grid)
+    if ((int64_t)((g.bid * blockDim.x) >> 5) >= (int64_t)total) return;
+    for (int i = threadIdx.x; i < kLut; i += blockDim.x) s_lut[i] = n.lut_p[i];
+    __syncthreads();
     const int32_t *ring = n.ring_ids + (size_t)slot * n.N;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t warps = part_threads(g) >> 5;
     const bool compact = n.rin32 != nullptr;
     int32_t *nb = s_nb[warp];
+    bool wrote = false;                           // this thread added into sd_rev
     auto spiker = [&](uint32_t item) -> int32_t {
         return (int)item < ce ? ring[item] : ring[n.N - 1 - ((int)item - ce)];
     };
@@ -630,12 +674,16 @@ __device__ __forceinline__ void ltp_body(const DevNet &n, const int *t_now, int 
                 const int lag = recent ? (__ffs(recent) - 1 - (int)d) : (tp - (int)h[u].y - (int)d);
                 if (lag < kLut) {
                     const int32_t a = s_lut[lag];
-                    if (a) red_add(&n.sd_rev[e0 + 32 * u], a);   // coalesced: the target's entries are contiguous
+                    if (a) {
+                        red_add(&n.sd_rev[e0 + 32 * u], a);   // coalesced: the target's entries are contiguous
+                        wrote = true;
+                    }
                 }
             }
         }
         __syncwarp();
     }
+    if (__any_sync(0xffffffffu, wrote) && lane == 0) n.ctr->sd_rev_dirty = 1;
 }
 
 // ---------------------------------------------------------------------------
@@ -652,6 +700,10 @@ __device__ __forceinline__ void fold_body(const DevNet &n, const int *t_now, int
     // the targets in flight form a narrow band of the torus and so do the
     // source rows their synapses scatter into: the scatter stays in L2.  A
     // warp takes one target at a time, four entries per lane in flight.
+    // nothing to fold when no potentiation was accumulated since the last
+    // fold (every block sees the same flag: it is cleared only after all of
+    // them have finished)
+    if (!*(volatile int *)&n.ctr->sd_rev_dirty) return;
     __shared__ uint32_t s_chunk;
     __shared__ int32_t s_nb[32][kSlotStride];
     constexpr uint32_t kFoldTargets = 64;
@@ -705,6 +757,13 @@ __device__ __forceinline__ void fold_body(const DevNet &n, const int *t_now, int
         if (threadIdx.x == 0) s_chunk = (g.nblk + atomicAdd(&n.ctr->fold_cursor, 1u)) * kFoldTargets;
         __syncthreads();
         c0 = s_chunk;
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&n.ctr->fold_done, 1u) == g.nblk - 1) {
+            n.ctr->sd_rev_dirty = 0;
+            n.ctr->fold_done = 0;
+        }
     }
 }
 

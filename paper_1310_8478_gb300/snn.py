@@ -67,7 +67,7 @@ class SnnLaunch(ctypes.Structure):
                 ("ltp_blocks_per_sm", ctypes.c_uint32), ("deriv_block", ctypes.c_uint32),
                 ("graph_steps", ctypes.c_uint32), ("dense_block", ctypes.c_uint32),
                 ("dense_rows", ctypes.c_uint32), ("dense_permille", ctypes.c_uint32),
-                ("staged_permille", ctypes.c_uint32)]
+                ("staged_permille", ctypes.c_uint32), ("ring_permille", ctypes.c_uint32)]
 
 
 class SnnProfile(ctypes.Structure):

@@ -45,7 +45,7 @@ def test_config_struct_layout_matches_header():
     assert c.a_plus_mv.offset == 56 and c.seed.offset == 112 and c.raster_capacity.offset == 128
     assert ctypes.sizeof(c) == 136
     assert ctypes.sizeof(snn.SnnCounters) == 64
-    assert ctypes.sizeof(snn.SnnLaunch) == 44
+    assert ctypes.sizeof(snn.SnnLaunch) == 48
     assert ctypes.sizeof(snn.SnnProfile) == 128
 
 

@@ -7,8 +7,9 @@ grid8_m1125_digests.json: at every checkpoint the event counters, the sha256
 of the raster since the previous checkpoint and, at some, the sha256 of w
 and sd in canonical order.  The CUDA path must reproduce every one of them,
 bit for bit, in each way of taking the steps: the device's own choice, the
-event-driven delivery only, the 13-column staged delivery, and the dense
-pass whenever anything fired.  The run crosses the update that closes step
+event-driven deliveries only, the column walk only, the ring-list delivery
+only, the 13-column staged delivery, and the dense pass whenever anything
+fired.  The run crosses the update that closes step
 999 (paper Table 2, "long term synaptic plasticity") while nearly every
 neuron fires every step, so the dense pass's long-term-update branch and the
 fold of the event-driven potentiation run on full 1128-slot rows of a torus
@@ -29,7 +30,9 @@ pytestmark = pytest.mark.gpu
 MODES = {"auto": None,
          "sparse": dict(dense_permille=1001, staged_permille=0xffffffff),
          "staged": dict(dense_permille=1001, staged_permille=1),
-         "dense": dict(dense_permille=1)}
+         "dense": dict(dense_permille=1),
+         "ordered": dict(dense_permille=1001, staged_permille=0xffffffff, ring_permille=1),
+         "ring": dict(dense_permille=1001, staged_permille=0xffffffff, ring_permille=0xffffffff)}
 
 
 def _sha(a):

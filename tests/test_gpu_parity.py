@@ -25,7 +25,11 @@ def eng():
 MODES = {"auto": None,
          "sparse": dict(dense_permille=1001, staged_permille=0xffffffff),
          "staged": dict(dense_permille=1001, staged_permille=1),
-         "dense": dict(dense_permille=1)}
+         "dense": dict(dense_permille=1),
+         # the column walk in every event-driven step, and the ring-list
+         # delivery in every one
+         "ordered": dict(dense_permille=1001, staged_permille=0xffffffff, ring_permille=1),
+         "ring": dict(dense_permille=1001, staged_permille=0xffffffff, ring_permille=0xffffffff)}
 
 
 def gpu_net(eng, cfg, mode="auto", **kw):
@@ -84,7 +88,7 @@ def test_generated_network_equals_oracle(eng, orc, cfg):
 # ---------------------------------------------------------------------------
 # whole runs, bit-exact
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("mode", ["auto", "sparse", "staged", "dense"])
+@pytest.mark.parametrize("mode", ["auto", "sparse", "staged", "dense", "ordered", "ring"])
 def test_col1_m100_full_second_bitexact(eng, orc, mode):
     cfg = workloads.workload("col1_m100")
     o = orc.Oracle(cfg)
@@ -97,7 +101,7 @@ def test_col1_m100_full_second_bitexact(eng, orc, mode):
             assert n.profile()["dense_steps"] > 300
 
 
-@pytest.mark.parametrize("mode", ["auto", "sparse", "staged", "dense"])
+@pytest.mark.parametrize("mode", ["auto", "sparse", "staged", "dense", "ordered", "ring"])
 @pytest.mark.parametrize("gx,gy,m,T,seed", [
     (2, 2, 60, 1100, 31),        # ring members coincide on a 2x2 torus; crosses a derivative update
     (3, 3, 100, 1050, 32),
@@ -132,7 +136,7 @@ DEGENERATE = {
 }
 
 
-@pytest.mark.parametrize("mode", ["auto", "sparse", "staged", "dense"])
+@pytest.mark.parametrize("mode", ["auto", "sparse", "staged", "dense", "ordered", "ring"])
 @pytest.mark.parametrize("name", sorted(DEGENERATE))
 def test_degenerate_networks_bitexact(eng, orc, name, mode):
     cfg = workloads.custom(**DEGENERATE[name])
@@ -170,7 +174,7 @@ def grid8_onset(orc):
     return o
 
 
-@pytest.mark.parametrize("mode", ["auto", "sparse", "staged", "dense"])
+@pytest.mark.parametrize("mode", ["auto", "sparse", "staged", "dense", "ordered", "ring"])
 def test_grid8_m1125_onset_bitexact(eng, grid8_onset, mode):
     with gpu_net(eng, workloads.workload("grid8_m1125"), mode) as n:
         n.run(32)
@@ -178,7 +182,7 @@ def test_grid8_m1125_onset_bitexact(eng, grid8_onset, mode):
         assert n.counters()["spikes"] > 100000
 
 
-@pytest.mark.parametrize("mode", ["sparse", "staged", "dense"])
+@pytest.mark.parametrize("mode", ["sparse", "staged", "dense", "ordered", "ring"])
 @pytest.mark.parametrize("flag_pair", [("STDP_OFF", 1, 1), ("DELIVERY_OFF", 2, 2)])
 def test_debug_flags_bitexact(eng, orc, flag_pair, mode):
     _, of, gf = flag_pair
@@ -393,3 +397,24 @@ def test_reset_restarts_the_same_run(eng):
         n.run(1100)
         r2, w2 = n.raster(), n.weights()
         assert np.array_equal(r1[1], r2[1]) and np.array_equal(w1[1], w2[1])
+
+
+def test_repeated_runs_are_identical(eng):
+    # the same net run three times (CUDA graphs, then eager steps) gives the
+    # same raster, weights and derivatives: no result may depend on the
+    # order in which threads or blocks happen to run (a 19x19 torus of the
+    # serving mix, across a long-term update)
+    cfg = workloads.custom(grid_x=19, grid_y=19, fanout=100, pct_ring=(40, 30, 20, 10), seed=5004)
+    runs = []
+    for shape in (None, None, dict(graph_steps=1)):
+        with gpu_net(eng, cfg, raster_capacity=19 * 19 * 1250 * 1400) as n:
+            if shape:
+                n.set_launch(**shape)
+            n.run(1400)
+            t, g = n.raster()
+            w, sd = n.weights()
+            runs.append((t, g, w, sd, n.counters()["e_all"]))
+    for r in runs[1:]:
+        for a, b in zip(r[:4], runs[0][:4]):
+            assert np.array_equal(a, b)
+        assert r[4] == runs[0][4]

@@ -28,7 +28,8 @@ def test_profile_counts_every_kernel_and_keeps_results(eng, orc):
         # make the column-staged delivery eligible, so that a step launches
         # the five step kernels k_ltp, k_deliver_ordered, k_deliver_cols,
         # k_dense, k_neuron_f32, and the step closing a period also k_fold
-        # and k_deriv
+        # and k_deriv (the ring-list delivery of compact nets is off by
+        # default and not launched)
         n.set_launch(staged_permille=1)
         n.run(T0)
         n.set_profile(True)
