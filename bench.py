@@ -640,6 +640,14 @@ def main():
         dram = traffic * dd["dense_steps"] / (kernel_ms[dom] / 1000.0) / 1e9
         roofline["dram_achieved"] = round(dram, 1)
         roofline["dram_frac"] = round(dram / peak, 4)
+    elif traffic is not None and prof[dom][0] > 0:
+        # the committed capture's DRAM bytes per launch (the same timed steps
+        # of the same workload) over this run's time of the kernel: what it
+        # really moves, next to its algorithmic bytes
+        dram = traffic * prof[dom][0] / (kernel_ms[dom] / 1000.0) / 1e9
+        roofline["dram_achieved"] = round(dram, 1)
+        roofline["dram_frac"] = round(dram / peak, 4)
+        roofline["traffic_vs_algorithmic"] = round(traffic * prof[dom][0] / max(alg[dom], 1.0), 4)
     if atomics is not None and prof["deliver"][1] > 0:
         # events delivered by the event-driven kernels per second of their
         # time, against the measured rate of scattered L2 reductions (one per
