@@ -139,6 +139,11 @@ struct snn_net {
     // stimulus
     size_t stim_cap = 0;
     int64_t stim_off_cap = 0;
+    // pinned host memory: the counters read after a run ([1]) and before one
+    // ([0]), and the staging of a stimulus upload
+    DevCounters *host_ctr = nullptr;
+    char *stim_stage = nullptr;
+    size_t stim_stage_cap = 0;
     // host state
     int32_t t = 0;
     snn_launch launch{};
@@ -659,6 +664,7 @@ int cuda_init(snn_net *net, void *cuda_stream)
         SNN_CUDA(cudaStreamCreateWithFlags(&net->stream, cudaStreamNonBlocking));
         net->own_stream = true;
     }
+    SNN_CUDA(cudaHostAlloc(&net->host_ctr, 2 * sizeof(DevCounters), cudaHostAllocDefault));
     return SNN_OK;
 }
 
@@ -816,8 +822,11 @@ int read_counters_raw(snn_net *net, DevCounters *hc)
     return SNN_OK;
 }
 
+// end of a run: the counters are copied out behind the steps and read after
+// the one synchronisation (the device error word decides the return code)
 int finish_run(snn_net *net)
 {
+    SNN_CUDA(cudaMemcpyAsync(&net->host_ctr[1], net->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, net->stream));
     SNN_CUDA(cudaStreamSynchronize(net->stream));
     SNN_CUDA(cudaGetLastError());
     if (net->profile && net->ev_used) {
@@ -829,8 +838,7 @@ int finish_run(snn_net *net)
         }
         net->ev_used = 0;
     }
-    DevCounters hc{};
-    SNN_TRY(read_counters_raw(net, &hc));
+    const DevCounters &hc = net->host_ctr[1];
     if (hc.error) {
         set_error("device error word %d", hc.error);
         return (hc.error == SNN_ETIMEOUT || hc.error == SNN_EBOUNDS) ? hc.error : SNN_ECUDA;
@@ -838,10 +846,15 @@ int finish_run(snn_net *net)
     return SNN_OK;
 }
 
-int run_steps(snn_net *net, uint32_t n_ms)
+// count_before: also copy the counters out ahead of the steps (host_ctr[0]),
+// without a synchronisation of its own
+int run_steps(snn_net *net, uint32_t n_ms, bool count_before = false)
 {
     if ((int64_t)net->t + n_ms > 0x7fff0000ll) { set_error("time limit reached"); return SNN_ESTATE; }
     SNN_TRY(ensure_raster_steps(net, (int64_t)net->t + n_ms + 2 - net->dn.raster_t0));
+    if (count_before)
+        SNN_CUDA(cudaMemcpyAsync(&net->host_ctr[0], net->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost,
+                                 net->stream));
     const uint32_t L = effective_graph_len(net);
     if (L != net->graph_len) {
         drop_graphs(net);
@@ -918,16 +931,32 @@ int set_stimulus_impl(snn_net *net, const snn_stimulus *ev, size_t n)
         drop_graphs(net);
         return SNN_OK;
     }
-    std::stable_sort(e.begin(), e.end(), [](const snn_stimulus &a, const snn_stimulus &b) { return a.t < b.t; });
+    auto by_t = [](const snn_stimulus &a, const snn_stimulus &b) { return a.t < b.t; };
+    if (!std::is_sorted(e.begin(), e.end(), by_t)) std::stable_sort(e.begin(), e.end(), by_t);
     const int32_t t0 = e.front().t, t1 = e.back().t + 1;
-    std::vector<int32_t> gid(e.size()), q(e.size());
-    std::vector<int64_t> off((size_t)(t1 - t0) + 1, 0);
+    // staged in pinned host memory (the copies below run behind the caller;
+    // the stream is idle here, every run ends with a synchronisation, so the
+    // staging of an earlier upload is free)
+    const size_t n_off = (size_t)(t1 - t0) + 1;
+    const size_t stage = e.size() * 8 + n_off * 8;
+    SNN_CUDA(cudaStreamSynchronize(net->stream));
+    if (stage > net->stim_stage_cap) {
+        if (net->stim_stage) cudaFreeHost(net->stim_stage);
+        net->stim_stage = nullptr;
+        net->stim_stage_cap = 0;
+        SNN_CUDA(cudaHostAlloc(&net->stim_stage, stage, cudaHostAllocDefault));
+        net->stim_stage_cap = stage;
+    }
+    int64_t *off = reinterpret_cast<int64_t *>(net->stim_stage);
+    int32_t *gid = reinterpret_cast<int32_t *>(off + n_off);
+    int32_t *q = gid + e.size();
+    std::fill(off, off + n_off, 0);
     for (size_t i = 0; i < e.size(); ++i) {
         gid[i] = e[i].gid;
         q[i] = e[i].q16;
         off[(size_t)(e[i].t - t0) + 1]++;
     }
-    for (size_t k = 1; k < off.size(); ++k) off[k] += off[k - 1];
+    for (size_t k = 1; k < n_off; ++k) off[k] += off[k - 1];
     if (e.size() > net->stim_cap) {
         dfree(net, (void *)dn.stim_gid);
         dfree(net, (void *)dn.stim_q16);
@@ -939,18 +968,17 @@ int set_stimulus_impl(snn_net *net, const snn_stimulus *ev, size_t n)
         dn.stim_q16 = b;
         net->stim_cap = e.size();
     }
-    if ((int64_t)off.size() > net->stim_off_cap) {
+    if ((int64_t)n_off > net->stim_off_cap) {
         dfree(net, (void *)dn.stim_off);
         dn.stim_off = nullptr;
         int64_t *o = nullptr;
-        SNN_TRY(dalloc_t(net, off.size(), &o));
+        SNN_TRY(dalloc_t(net, n_off, &o));
         dn.stim_off = o;
-        net->stim_off_cap = (int64_t)off.size();
+        net->stim_off_cap = (int64_t)n_off;
     }
-    SNN_CUDA(cudaMemcpyAsync((void *)dn.stim_gid, gid.data(), gid.size() * 4, cudaMemcpyHostToDevice, net->stream));
-    SNN_CUDA(cudaMemcpyAsync((void *)dn.stim_q16, q.data(), q.size() * 4, cudaMemcpyHostToDevice, net->stream));
-    SNN_CUDA(cudaMemcpyAsync((void *)dn.stim_off, off.data(), off.size() * 8, cudaMemcpyHostToDevice, net->stream));
-    SNN_CUDA(cudaStreamSynchronize(net->stream));
+    SNN_CUDA(cudaMemcpyAsync((void *)dn.stim_gid, gid, e.size() * 4, cudaMemcpyHostToDevice, net->stream));
+    SNN_CUDA(cudaMemcpyAsync((void *)dn.stim_q16, q, e.size() * 4, cudaMemcpyHostToDevice, net->stream));
+    SNN_CUDA(cudaMemcpyAsync((void *)dn.stim_off, off, n_off * 8, cudaMemcpyHostToDevice, net->stream));
     dn.stim_t0 = t0;
     dn.stim_t1 = t1;
     drop_graphs(net);
@@ -1045,6 +1073,8 @@ void snn_free(snn_net *net)
     drop_graphs(net);
     for (cudaEvent_t e : net->ev_pool) cudaEventDestroy(e);
     while (!net->blocks.empty()) dfree(net, net->blocks.back().p);
+    if (net->host_ctr) cudaFreeHost(net->host_ctr);
+    if (net->stim_stage) cudaFreeHost(net->stim_stage);
     if (net->own_stream && net->stream) cudaStreamDestroy(net->stream);
     delete net;
 }
@@ -1317,11 +1347,10 @@ int snn_run_host(snn_net *net, uint32_t n_ms, const snn_stimulus *host_stimulus,
     const int32_t t0 = net->t;
     SNN_TRY(set_stimulus_impl(net, host_stimulus, host_stimulus ? n_stim : 0));
     if (!host_spikes) {
-        DevCounters a{}, b{};
-        SNN_TRY(read_counters_raw(net, &a));
-        SNN_TRY(run_steps(net, n_ms));
-        SNN_TRY(read_counters_raw(net, &b));
-        if (n_out) *n_out = (size_t)(b.spikes - a.spikes);
+        // one synchronisation: the counters before and after the steps are
+        // copied out on the stream around them
+        SNN_TRY(run_steps(net, n_ms, true));
+        if (n_out) *n_out = (size_t)(net->host_ctr[1].spikes - net->host_ctr[0].spikes);
         return SNN_OK;
     }
     if (!net->dn.raster_gid) { set_error("snn_run_host needs raster_capacity > 0"); return SNN_ESTATE; }

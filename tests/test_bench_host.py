@@ -41,6 +41,26 @@ def test_kernel_source_digest_tracks_the_right_files():
     assert bench.kernel_source_digest("deliver_ordered") == d_step
 
 
+def test_end_to_end_read_back_bytes_are_the_counter_block(tmp_path):
+    """The end-to-end leg states its device-to-host bytes per step as two
+    copies of the device counter block (before and after the step, inside
+    snn_run_host): the constant must be that block's size as compiled."""
+    import shutil
+    import subprocess
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not found")
+    src = tmp_path / "sz.cu"
+    src.write_text('#include "snn_internal.cuh"\n#include <cstdio>\n'
+                   'int main() { std::printf("%zu\\n", sizeof(snn::DevCounters)); return 0; }\n')
+    exe = tmp_path / "sz"
+    subprocess.run([nvcc, "-std=c++17", "-I", os.path.join(ROOT, "include"),
+                    "-I", os.path.join(ROOT, "paper_1310_8478_gb300", "csrc"), "-o", str(exe), str(src)],
+                   check=True, capture_output=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    assert int(out) == bench.DEVICE_COUNTERS_BYTES
+
+
 def test_clock_samples_are_summarised(tmp_path):
     path = tmp_path / "clocks.csv"
     path.write_text("1965, 2070, 900.1, Not Active, Not Active, Not Active, Active\n"

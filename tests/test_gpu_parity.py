@@ -388,6 +388,32 @@ def test_host_thalamic_events_reproduce_the_internal_drive(eng):
         assert np.array_equal(wa[0], wb[0]) and np.array_equal(wa[1], wb[1])
 
 
+def test_run_host_counts_one_step_at_a_time(eng):
+    # the end-to-end pattern of one call per step: each call's stimulus is
+    # that step's drive (given in reverse order, so the library sorts it)
+    # and each call returns that step's spike count; the run equals the
+    # net's own drive, and a stimulus set on its own then run equals it too
+    cfg = workloads.custom(grid_x=3, grid_y=2, fanout=150, pct_ring=(40, 30, 20, 10), seed=65)
+    from paper_1310_8478_gb300 import snn
+    T = 60
+    with gpu_net(eng, cfg) as a, gpu_net(eng, cfg) as b, gpu_net(eng, cfg) as c:
+        a.run(T)
+        ta, ga = a.raster()
+        b.set_thalamic(False)
+        c.set_thalamic(False)
+        ev = snn.snn_thalamic_events(cfg, 0, T)
+        per = len(ev) // T
+        for t in range(T):
+            got = b.run_host_counts(1, ev[t * per:(t + 1) * per][::-1])
+            assert got == int(np.count_nonzero(ta == t)), t
+        c.set_stimulus(ev["t"], ev["gid"], ev["q16"])
+        c.run(T)
+        for n in (b, c):
+            tb, gb = n.raster()
+            assert np.array_equal(ta, tb) and np.array_equal(ga, gb)
+            assert n.counters()["e_all"] == a.counters()["e_all"]
+
+
 def test_reset_restarts_the_same_run(eng):
     cfg = workloads.custom(grid_x=2, grid_y=2, fanout=100, pct_ring=(40, 30, 20, 10), seed=64)
     with gpu_net(eng, cfg) as n:
