@@ -198,7 +198,9 @@ int snn_build_network_explicit(const snn_config *cfg, const int64_t *host_row_of
  * be 0 to clear), applied in S2 of their step before the neuron update.  The
  * thalamic drive of Sec. 2 / Table 2 ("thalamic input") is separate and
  * always on unless thal_per_col_per_ms = 0.  Events before the current step
- * are ignored.  SNN_EINVAL if a gid is out of range.
+ * are ignored.  SNN_EINVAL if a gid is out of range.  The events are staged
+ * in library-owned pinned memory and copied on the net's stream: the call
+ * may return before the copy ends, and the caller's array is free at once.
  */
 int snn_set_stimulus(snn_net *net, const snn_stimulus *host_events, size_t n);
 
@@ -266,7 +268,9 @@ int snn_run(snn_net *net, uint32_t n_ms);
  * host_spikes is not NULL, copies the spikes of those steps, sorted by
  * (t, gid), into host_spikes (capacity cap) and resets the device raster.
  * *n_out = spikes emitted in the window.  SNN_ETRUNC if cap is too small (the
- * simulation still advanced) or the device raster overflowed.
+ * simulation still advanced) or the device raster overflowed.  Without
+ * host_spikes the call synchronises with the stream once: the counters are
+ * copied out before and after the steps into pinned memory on the stream.
  */
 int snn_run_host(snn_net *net, uint32_t n_ms, const snn_stimulus *host_stimulus, size_t n_stim,
                  snn_spike *host_spikes, size_t cap, size_t *n_out);
