@@ -495,8 +495,6 @@ def main():
         t_build = time.perf_counter() - t_build
         device_bytes = net.device_bytes
         net.run(W)
-        net.set_profile(True)
-        prof0 = net.profile()
         c0 = net.counters()
         clocks = ClockSampler(local_rank)
         barrier()
@@ -511,10 +509,32 @@ def main():
         clk = clocks.stop()
         ms = e0.elapsed_time(e1)
         c1 = net.counters()
+        device_digest = raster_digest(net, W, W + K) if c1["raster_dropped"] == 0 else None
+
+        # the kernels of the same steps, timed one by one: the net restarted
+        # and the same steps run again with profiling on, in which the library
+        # launches the step's kernels one after another, each between CUDA
+        # events on its own stream (in the timed run above the potentiation
+        # overlaps the delivery on a side stream, so their own durations
+        # would count each other's time)
+        net.reset()
+        net.run(W)
+        net.set_profile(True)
+        prof0 = net.profile()
+        cp0 = net.counters()
+        torch.cuda.synchronize()
+        p0 = torch.cuda.Event(enable_timing=True)
+        p1 = torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        net.run(K)
+        p1.record(stream)
+        torch.cuda.synchronize()
+        ms_profiled = p0.elapsed_time(p1)
+        cp1 = net.counters()
         prof = net.profile()
         prof1 = prof
         net.set_profile(False)
-        device_digest = raster_digest(net, W, W + K) if c1["raster_dropped"] == 0 else None
+        profiled_same_events = (cp1["e_all"] - cp0["e_all"]) == (c1["e_all"] - c0["e_all"])
 
         # end-to-end leg: the same workload restarted, driven from host memory
         # (the thalamic events of every step are copied in from pinned host
@@ -674,6 +694,8 @@ def main():
         "raster": {"capacity": raster_cap, "dropped": c1["raster_dropped"]},
         "roofline": roofline,
         "kernels": per_kernel,
+        "kernels_timed_in": {"what": "the same steps again from a reset, profiled: kernels one after another",
+                             "ms_per_step": round(ms_profiled / K, 5), "same_events": bool(profiled_same_events)},
         "gpu_launches": int(prof1["kernels"] - prof0["kernels"]),
         "build_s": round(t_build, 2),
         "e2e": e2e,

@@ -101,6 +101,11 @@ struct snn_net {
     int sm_count = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    // the potentiation owed by the last step runs on a side stream beside
+    // the delivery of the next one (they touch disjoint data), forked from
+    // and joined back into `stream` in every step that closes no period
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     bool explicit_net = false;
     GenParams gen{};
     DevNet dn{};
@@ -665,6 +670,9 @@ int cuda_init(snn_net *net, void *cuda_stream)
         net->own_stream = true;
     }
     SNN_CUDA(cudaHostAlloc(&net->host_ctr, 2 * sizeof(DevCounters), cudaHostAllocDefault));
+    SNN_CUDA(cudaStreamCreateWithFlags(&net->side, cudaStreamNonBlocking));
+    SNN_CUDA(cudaEventCreateWithFlags(&net->ev_fork, cudaEventDisableTiming));
+    SNN_CUDA(cudaEventCreateWithFlags(&net->ev_join, cudaEventDisableTiming));
     return SNN_OK;
 }
 
@@ -717,8 +725,16 @@ void launch_flush(snn_net *net)
 }
 
 // exact_t: t is the step itself (an eager launch), not only its parity (a
-// launch captured into a graph that serves many chunks of steps); the host
-// then leaves out the long-term update's kernels in steps that close no period
+// launch captured into a graph that serves many chunks of steps; the host
+// captures and replays graphs only over chunks in which no step closes a
+// period).  A step that closes a period runs its kernels one after another:
+// potentiation, the long-term update (which reads the folded potentiation
+// and changes the weights the delivery reads), delivery.  Any other step runs
+// the potentiation owed by step t - 1 on the side stream beside the delivery
+// of step t: one reads the histories and reverse index and accumulates into
+// sd_rev, the other reads the weights and accumulates into I and sd.  While
+// profiling, every step runs its kernels one after another, so that each
+// kernel's CUDA-event time is its own.
 void launch_step(snn_net *net, int32_t t, cudaStream_t s, bool exact_t)
 {
     const DevNet &dn = net->dn;
@@ -727,30 +743,37 @@ void launch_step(snn_net *net, int32_t t, cudaStream_t s, bool exact_t)
     const snn_launch &L = net->launch;
     const bool prof = net->profile;
     const uint32_t P = net->cfg.deriv_period_ms;
-    auto mark = [&](int kind) {
-        if (prof) cudaEventRecord(next_event(net, kind), s);
+    const bool closes = exact_t && P && t > 0 && (uint32_t)t % P == 0;
+    const bool fork = !closes && !prof;
+    cudaStream_t sl = fork ? net->side : s;        // the potentiation's stream
+    auto mark = [&](int kind, cudaStream_t on) {
+        if (prof) cudaEventRecord(next_event(net, kind), on);
     };
     // [S4(t-1) S5(t-1) S1(t)]: event-driven kernels and the dense pass; the
     // device picks one of the two (the other returns at once)
-    mark(2);
+    if (fork) {
+        cudaEventRecord(net->ev_fork, s);
+        cudaStreamWaitEvent(sl, net->ev_fork, 0);
+    }
+    mark(2, sl);
     // sparse grids follow the net's size (a warp per spiker / per 32 buckets)
     const int g_ltp = sized_grid(net, L.ltp_blocks_per_sm, net->N, L.ltp_block / 32);
     const int g_del = sized_grid(net, L.deliver_blocks_per_sm, (int64_t)net->N * dn.D / 4, L.deliver_block);
     int launched = 0;
-    k_ltp<<<g_ltp, L.ltp_block, 0, s>>>(dn, t_now, 0);
+    k_ltp<<<g_ltp, L.ltp_block, 0, sl>>>(dn, t_now, 0);
     ++launched;
-    mark(2);
-    // long-term update when t closes a period (decided on the device, so the
-    // same launches serve every step and graphs need no variants): the
-    // event-driven LTP is folded into sd first, both passes read sd afterwards
-    if (P && (!exact_t || (t > 0 && (uint32_t)t % P == 0))) {
-        mark(3);
+    mark(2, sl);
+    if (fork) cudaEventRecord(net->ev_join, sl);
+    // long-term update when t closes a period: the event-driven LTP is
+    // folded into sd first, both passes read sd afterwards
+    if (closes) {
+        mark(3, s);
         k_fold<<<sized_grid(net, 8, net->n_rin, 4096), 256, 0, s>>>(dn, t_now, 0);
         k_deriv<<<sized_grid(net, 8, (int64_t)dn.C * dn.ne, L.deriv_block / 32), L.deriv_block, 0, s>>>(dn, t_now, 0);
         launched += 2;
-        mark(3);
+        mark(3, s);
     }
-    mark(0);
+    mark(0, s);
     if (dn.ordered_ok) {
         k_deliver_ordered<<<net->ordered_grid, ordered_block(L.deliver_block),
                             ordered_smem_bytes(dn.npc, ordered_block(L.deliver_block)), s>>>(dn, t_now);
@@ -764,17 +787,18 @@ void launch_step(snn_net *net, int32_t t, cudaStream_t s, bool exact_t)
         k_deliver_cols<<<net->staged_grid, kStagedBlock, staged_smem_bytes(dn.npc, kStagedBlock), s>>>(dn, t_now);
         ++launched;
     }
-    mark(0);
+    mark(0, s);
     if (net->dense_ok) {
-        mark(4);
+        mark(4, s);
         k_dense<<<net->dense_grid, L.dense_block, dense_smem_bytes(dn.npc, L.dense_block), s>>>(dn, t_now);
         ++launched;
-        mark(4);
+        mark(4, s);
     }
+    if (fork) cudaStreamWaitEvent(s, net->ev_join, 0);
     // [S2(t) S3(t)]
     const int nb_neuron = (int)((net->N + L.neuron_block * kNeuronsPerThread - 1) /
                                 (L.neuron_block * kNeuronsPerThread));
-    mark(1);
+    mark(1, s);
     if (dn.vd) k_neuron_f64<<<nb_neuron, L.neuron_block, 0, s>>>(dn, t_now, t_next);
     else k_neuron_f32<<<nb_neuron, L.neuron_block, 0, s>>>(dn, t_now, t_next);
     ++launched;
@@ -782,7 +806,7 @@ void launch_step(snn_net *net, int32_t t, cudaStream_t s, bool exact_t)
         k_probe<<<(dn.probe_n + 255) / 256, 256, 0, s>>>(dn, t_now);
         ++launched;
     }
-    mark(1);
+    mark(1, s);
     if (prof) net->prof_kernels += launched;
 }
 
@@ -861,9 +885,12 @@ int run_steps(snn_net *net, uint32_t n_ms, bool count_before = false)
         net->graph_len = L;
     }
     uint32_t left = n_ms;
+    const uint32_t P = net->cfg.deriv_period_ms;
     while (left > 0) {
         const int32_t t = net->t;
-        if (L >= 2 && (t & 1) == 0 && left >= L) {
+        // the first step from t on that closes a period (t' > 0, t' % P == 0)
+        const int64_t closing = P ? std::max<int64_t>((int64_t)P, ((int64_t)t + P - 1) / P * P) : INT64_MAX;
+        if (L >= 2 && (t & 1) == 0 && left >= L && closing >= (int64_t)t + L) {
             if (net->graphs_dirty) {
                 for (int i = 0; i < 2; ++i)
                     if (net->graph[i]) { cudaGraphExecDestroy(net->graph[i]); net->graph[i] = nullptr; }
@@ -1074,6 +1101,9 @@ void snn_free(snn_net *net)
     for (cudaEvent_t e : net->ev_pool) cudaEventDestroy(e);
     while (!net->blocks.empty()) dfree(net, net->blocks.back().p);
     if (net->host_ctr) cudaFreeHost(net->host_ctr);
+    if (net->ev_fork) cudaEventDestroy(net->ev_fork);
+    if (net->ev_join) cudaEventDestroy(net->ev_join);
+    if (net->side) cudaStreamDestroy(net->side);
     if (net->stim_stage) cudaFreeHost(net->stim_stage);
     if (net->own_stream && net->stream) cudaStreamDestroy(net->stream);
     delete net;
