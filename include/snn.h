@@ -171,6 +171,9 @@ typedef struct snn_net snn_net;
  * delay-bucketed forward lists, the reverse (incoming excitatory) index and
  * the initial state (v = -65 mV, u = 0.2 v).
  *   cuda_stream: cudaStream_t the engine works on (NULL: a private stream).
+ *     The net also owns a side stream: in a step that closes no period the
+ *     potentiation owed by the last step runs there beside the delivery,
+ *     forked from and joined back into cuda_stream within the step.
  *   hbm_budget_bytes: upper bound of device memory the net may use (0: no bound).
  *   out: receives the handle.
  * Errors: SNN_EINVAL (bad cfg), SNN_ENOMEM (footprint above the budget or
@@ -256,8 +259,8 @@ int snn_step(snn_net *net);
 
 /*
  * snn_run -- advance n_ms steps (CUDA-graph replays of graph_steps steps where
- * the alignment allows, single steps otherwise); returns after completion and
- * the error-word check.
+ * the alignment allows and no step of the chunk closes a plasticity period,
+ * single steps otherwise); returns after completion and the error-word check.
  */
 int snn_run(snn_net *net, uint32_t n_ms);
 
@@ -355,7 +358,8 @@ int snn_read_counters(snn_net *net, snn_counters *out);
 int snn_net_info(const snn_net *net, uint32_t *n_neurons, int64_t *n_synapses,
                  size_t *device_bytes);
 
-/* snn_set_profile -- 1: time every kernel with CUDA events (no graphs); 0: off. */
+/* snn_set_profile -- 1: time every kernel with CUDA events (no graphs; the
+ * kernels of a step run one after another on the net's stream); 0: off. */
 int snn_set_profile(snn_net *net, int on);
 int snn_read_profile(snn_net *net, snn_profile *out);
 
