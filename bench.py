@@ -517,8 +517,14 @@ def main():
         # events on its own stream (in the timed run above the potentiation
         # overlaps the delivery on a side stream, so their own durations
         # would count each other's time)
+        # The launches of steps t0 .. t1 - 1 potentiate the spikers of steps
+        # t0 - 1 .. t1 - 2 (step t takes the potentiation owed by t - 1), so
+        # their potentiation visits are l_exc(t1 - 1) - l_exc(t0 - 1): the
+        # counters are read one step before each end of the region.
         net.reset()
-        net.run(W)
+        net.run(max(0, W - 1))
+        ca = net.counters()
+        net.run(W - max(0, W - 1))
         net.set_profile(True)
         prof0 = net.profile()
         cp0 = net.counters()
@@ -526,11 +532,14 @@ def main():
         p0 = torch.cuda.Event(enable_timing=True)
         p1 = torch.cuda.Event(enable_timing=True)
         p0.record(stream)
-        net.run(K)
+        net.run(K - 1)
+        cb = net.counters()
+        net.run(1)
         p1.record(stream)
         torch.cuda.synchronize()
         ms_profiled = p0.elapsed_time(p1)
         cp1 = net.counters()
+        ltp_visits = cb["l_exc"] - ca["l_exc"]
         prof = net.profile()
         prof1 = prof
         net.set_profile(False)
@@ -626,7 +635,7 @@ def main():
 
     d_events = c1["e_all"] - c0["e_all"]
     d_exc = c1["e_exc"] - c0["e_exc"]
-    d_ltp = c1["l_exc"] - c0["l_exc"]
+    d_ltp = ltp_visits
     d_spikes = c1["spikes"] - c0["spikes"]
     ms, total_events = combine_ranks(ms, d_events, dist, "cuda")
     if rank != 0:

@@ -204,8 +204,10 @@ class _FakeBenchNet:
         return out
 
     def counters(self):
+        # potentiation visits grow with the step (as over an onset): the
+        # visits of step s's spikers are 900 * (2 s + 1)
         return {"t": self.t, "spikes": 10 * self.t, "e_all": 2000 * self.t, "e_exc": 1500 * self.t,
-                "l_exc": 900 * self.t, "raster_dropped": 0}
+                "l_exc": 900 * self.t * self.t, "raster_dropped": 0}
 
     def reset(self):
         self.t = 0
@@ -290,6 +292,11 @@ def test_main_line_carries_every_key_with_a_fake_engine(monkeypatch, capsys):
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
     assert line["serve"]["requests"] == 4 and "p99_s" in line["serve"]["latency"]
     assert line["kernels"]["deriv"]["alg_gbs"] == 0.0                # no period closes in steps 3..7
+    # the launches of steps 3..7 potentiate the spikers of steps 2..6:
+    # 900 * (7^2 - 2^2) visits, less the 500 per step the dense pass took,
+    # 12 B each, over the fake's 0.02 ms per launch
+    assert line["kernels"]["ltp"]["alg_gbs"] == pytest.approx(
+        12.0 * (900 * (7 ** 2 - 2 ** 2) - 500 * 5) / (0.02 * 5 / 1000.0) / 1e9, abs=0.051)   # rounded to 0.1
     # the oracle is timed over the GPU leg's steps; the end-to-end leg
     # compares its raster with the device run's
     assert line["e2e"]["raster_sha256_equals_device_run"] is True
