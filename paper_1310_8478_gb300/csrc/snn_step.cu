@@ -30,6 +30,8 @@
 // bit-identical results because all synaptic arithmetic is int32 and the
 // per-synapse order of the updates is the same.  An LTP still owed when a run ends is applied
 // by the host-side flush (k_ltp + k_deriv with force = 1) before any read.
+#include <type_traits>
+
 #include "snn_internal.cuh"
 
 namespace snn {
@@ -559,6 +561,76 @@ __device__ __forceinline__ void deliver_ordered(const DevNet &n, const int *t_no
     deliver_cols<false>(n, t, s_lut, s_in, s_tile, s_ltd, s_hist, g, s_inh);
 }
 
+// One target's reverse entries [lo, hi), walked by a warp, kUnroll entries
+// per lane and round: the entries, then the sources' history words, then a
+// reduction of every non-zero amount into the entry's accumulator (no load:
+// an entry whose source did not fire inside the window costs its 4 or 8
+// bytes and nothing else).  The entries of the next round are loaded before
+// this round's histories are gathered, so that the two loads' latencies
+// overlap.  Returns whether the lane added into an accumulator.
+template <bool kCompact>
+__device__ __forceinline__ bool ltp_walk(const DevNet &n, int64_t lo, int64_t hi, int lane, const int32_t *nb,
+                                         const int32_t *s_lut, int tp)
+{
+    using Raw = typename std::conditional<kCompact, uint32_t, uint64_t>::type;
+    constexpr Raw kNone = ~(Raw)0;                // no entry (never a valid one: the delay is below 32)
+    auto load = [&](int64_t e) -> Raw {
+        if (e >= hi || out_of_range(n, e < n.n_rin)) return kNone;
+        if constexpr (kCompact) return n.rin32[e];
+        else return n.rin[e];
+    };
+    bool wrote = false;
+    Raw next[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) next[u] = load(lo + lane + 32 * u);
+    for (int64_t e0 = lo + lane; e0 < hi; e0 += 32 * kUnroll) {
+        Raw r[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            r[u] = next[u];
+            next[u] = load(e0 + 32 * (kUnroll + u));
+        }
+        uint2 h[kUnroll];
+        uint32_t dl[kUnroll];
+        bool ok[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            ok[u] = r[u] != kNone;
+            if (!ok[u]) continue;
+            uint32_t src;
+            if constexpr (kCompact) {
+                const uint32_t v = r[u] & 0xffffu;
+                const uint32_t sl = __umulhi(v, n.npc_recip);
+                src = (uint32_t)nb[sl] * n.npc + (v - sl * n.npc);
+                dl[u] = (r[u] >> 16) & 31u;
+            } else {
+                src = (uint32_t)r[u];
+                dl[u] = (uint32_t)(r[u] >> 48);
+            }
+            if (out_of_range(n, src < n.N)) {
+                ok[u] = false;
+                continue;
+            }
+            h[u] = n.hl[src];
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            if (!ok[u]) continue;
+            const uint32_t d = dl[u];
+            const uint32_t recent = h[u].x & (0xffffffffu << d);
+            const int lag = recent ? (__ffs(recent) - 1 - (int)d) : (tp - (int)h[u].y - (int)d);
+            if (lag < kLut) {
+                const int32_t a = s_lut[lag];
+                if (a) {
+                    red_add(&n.sd_rev[e0 + 32 * u], a);   // coalesced: the target's entries are contiguous
+                    wrote = true;
+                }
+            }
+        }
+    }
+    return wrote;
+}
+
 // ---------------------------------------------------------------------------
 // sparse S4 for step t - 1: warp per neuron that fired at t - 1; lanes walk
 // its incoming excitatory synapses.  The nearest arrival with t_pre + d <=
@@ -635,52 +707,8 @@ __device__ __forceinline__ void ltp_body(const DevNet &n, const int *t_now, int 
             hi2 = n.rin_off[p + 1];
             nb2 = neighbours(p);
         }
-        // kUnroll entries per lane: reverse entries, then the sources'
-        // histories, then a reduction of every non-zero amount into the
-        // entry's accumulator (no load: an entry whose source did not fire
-        // inside the window costs its 4 or 8 bytes and nothing else)
-        for (int64_t e0 = lo + lane; e0 < hi; e0 += 32 * kUnroll) {
-            uint32_t src[kUnroll], dl[kUnroll];
-            bool ok[kUnroll];
-#pragma unroll
-            for (int u = 0; u < kUnroll; ++u) {
-                const int64_t e = e0 + 32 * u;
-                ok[u] = e < hi && !out_of_range(n, e < n.n_rin);
-                if (!ok[u]) continue;
-                if (compact) {
-                    const uint32_t r = n.rin32[e];
-                    const uint32_t v = r & 0xffffu;
-                    const uint32_t sl = __umulhi(v, n.npc_recip);
-                    src[u] = (uint32_t)nb[sl] * n.npc + (v - sl * n.npc);
-                    dl[u] = (r >> 16) & 31u;
-                } else {
-                    const uint64_t r = n.rin[e];
-                    src[u] = (uint32_t)r;
-                    dl[u] = (uint32_t)(r >> 48);
-                }
-                if (out_of_range(n, src[u] < n.N)) ok[u] = false;
-            }
-            uint2 h[kUnroll];
-#pragma unroll
-            for (int u = 0; u < kUnroll; ++u) {
-                if (!ok[u]) continue;
-                h[u] = n.hl[src[u]];
-            }
-#pragma unroll
-            for (int u = 0; u < kUnroll; ++u) {
-                if (!ok[u]) continue;
-                const uint32_t d = dl[u];
-                const uint32_t recent = h[u].x & (0xffffffffu << d);
-                const int lag = recent ? (__ffs(recent) - 1 - (int)d) : (tp - (int)h[u].y - (int)d);
-                if (lag < kLut) {
-                    const int32_t a = s_lut[lag];
-                    if (a) {
-                        red_add(&n.sd_rev[e0 + 32 * u], a);   // coalesced: the target's entries are contiguous
-                        wrote = true;
-                    }
-                }
-            }
-        }
+        if (compact) wrote |= ltp_walk<true>(n, lo, hi, lane, nb, s_lut, tp);
+        else wrote |= ltp_walk<false>(n, lo, hi, lane, nb, s_lut, tp);
         __syncwarp();
     }
     if (__any_sync(0xffffffffu, wrote) && lane == 0) n.ctr->sd_rev_dirty = 1;
