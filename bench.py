@@ -413,16 +413,30 @@ def serve_leg(n_requests: int, rate: float, budget_gb: float, stream, one_at_a_t
         # the same requests, each run alone to completion one after another
         # (no waiting for arrivals), wall time around the whole sequence
         ev1 = 0
+        by_kind = {}
         t0 = time.perf_counter()
         for r in reqs:
+            tr = time.perf_counter()
             n = serve.snn.Network(r.cfg, stream=stream, hbm_budget_bytes=int(budget_gb * 1e9), raster_capacity=0)
             try:
                 n.run(r.duration_ms)
-                ev1 += n.counters()["e_all"]
+                e = n.counters()["e_all"]
+                ev1 += e
             finally:
                 n.close()
+            side = r.cfg["grid_x"]
+            kind = "M=%d, side %s" % (r.cfg["fanout"], "1-8" if side <= 8 else ("9-16" if side <= 16 else "17-32"))
+            k = by_kind.setdefault(kind, {"requests": 0, "s": 0.0, "events": 0})
+            k["requests"] += 1
+            k["s"] += time.perf_counter() - tr
+            k["events"] += e
         wall1 = time.perf_counter() - t0
+        for k in by_kind.values():
+            k["share"] = round(k["s"] / wall1, 4)
+            k["events_per_s"] = k["events"] / max(k["s"], 1e-9)
+            k["s"] = round(k["s"], 3)
         out["one_at_a_time"] = {"value": ev1 / wall1, "wall_s": wall1, "same_events": ev1 == ev}
+        out["one_at_a_time_by_kind"] = dict(sorted(by_kind.items()))
         out["speedup"] = (ev / wall) / (ev1 / wall1)
     return out
 
