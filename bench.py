@@ -523,7 +523,12 @@ def main():
         clk = clocks.stop()
         ms = e0.elapsed_time(e1)
         c1 = net.counters()
-        device_digest = raster_digest(net, W, W + K) if c1["raster_dropped"] == 0 else None
+        # the raster digest reads the window's spikes to the host: skipped
+        # for windows of more than RASTER_DIGEST_MAX_SPIKES spikes (the full
+        # 2000-step run holds ~1e10), where the counters are compared alone
+        device_digest = (raster_digest(net, W, W + K)
+                         if c1["raster_dropped"] == 0 and c1["spikes"] - c0["spikes"] <= RASTER_DIGEST_MAX_SPIKES
+                         else None)
 
         # the kernels of the same steps, timed one by one: the net restarted
         # and the same steps run again with profiling on, in which the library
@@ -588,7 +593,7 @@ def main():
                    "d2h_bytes_per_step": 2 * DEVICE_COUNTERS_BYTES, "steps": KE,
                    "same_events_as_device_run": bool(ce1["e_all"] - ce0["e_all"] == c1["e_all"] - c0["e_all"]
                                                      and KE == K)}
-            if KE == K and device_digest is not None and ce1["raster_dropped"] == 0:
+            if KE == K and device_digest is not None and ce1["raster_dropped"] == 0:  # digest taken above
                 e2e["raster_sha256_equals_device_run"] = raster_digest(net, W, W + K) == device_digest
             net.set_thalamic(True)
 
@@ -803,6 +808,9 @@ def steady_leg(net, cfg, stream, n_neurons, args, dense_at: int = 60, n_dense: i
         out[name] = leg
     return out
 
+
+# largest window whose raster bench.py reads back for a digest (4 GB of host memory)
+RASTER_DIGEST_MAX_SPIKES = 500_000_000
 
 # bytes of the device counter block that snn_run_host copies to the host
 # before and after the steps it runs (its result: the spikes of the window)
