@@ -697,14 +697,26 @@ def main():
         roofline["traffic_vs_algorithmic"] = round(traffic * prof[dom][0] / max(alg[dom], 1.0), 4)
     if atomics is not None and prof["deliver"][1] > 0:
         # events delivered by the event-driven kernels per second of their
-        # time, against the measured rate of scattered L2 reductions (one per
-        # event on another column) and of shared atomics (own column)
+        # time, split by where they land: an event on another column is one
+        # scattered L2 reduction (the excitatory synapses outside the source
+        # column: 1 - pct_ring[0] of them, exact on tori of side >= 5), an
+        # event on the source column (every inhibitory one, the local share of
+        # the excitatory ones) a shared-memory atomic; each against its
+        # measured rate
         ev_sparse = d_events - dd["dense_events"]
-        roofline["atomic"] = {"kernel": "deliver", "events_per_s": round(ev_sparse / (prof["deliver"][1] / 1e3)),
-                              "red_global_window_per_s": round(atomics["red_global_window_gops"] * 1e9),
-                              "atom_shared_window_per_s": round(atomics["atom_shared_window_gops"] * 1e9),
-                              "frac_of_l2_reductions": round(ev_sparse / (prof["deliver"][1] / 1e3)
-                                                             / (atomics["red_global_window_gops"] * 1e9), 4)}
+        exc_sparse = d_exc - dd["dense_exc_events"]
+        secs_d = prof["deliver"][1] / 1e3
+        l2_red = exc_sparse * (1.0 - cfg["pct_ring"][0] / 100.0)
+        smem = ev_sparse - l2_red
+        red_rate = atomics["red_global_window_gops"] * 1e9
+        smem_rate = atomics["atom_shared_window_gops"] * 1e9
+        roofline["atomic"] = {"kernel": "deliver", "events_per_s": round(ev_sparse / secs_d),
+                              "red_global_window_per_s": round(red_rate),
+                              "atom_shared_window_per_s": round(smem_rate),
+                              "l2_reductions_per_s": round(l2_red / secs_d),
+                              "frac_of_l2_reduction_rate": round(l2_red / secs_d / red_rate, 4),
+                              "shared_atomics_per_s": round(smem / secs_d),
+                              "frac_of_shared_atomic_rate": round(smem / secs_d / smem_rate, 4)}
     line = {
         "metric": "synaptic events/s", "value": value, "unit": "events/s", "n_gpus": world, "steps": K,
         "warmup": W, "ms_per_step": ms / K, "higher_is_better": True,
