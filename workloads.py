@@ -52,6 +52,10 @@ WORKLOADS = {
     # 64x64 torus (5.12 M neurons, 5.76 G synapses), same mix
     "grid64_m1125": dict(grid_x=64, grid_y=64, fanout=1125, pct_ring=(40, 30, 20, 10),
                          seed=3, sim_ms=2000),
+    # the same 5.12 M neurons with 16 synapses each (82 M synapses, ~1.5 GB
+    # on the device): the neuron update at full width, for profiling
+    "grid64_m16": dict(grid_x=64, grid_y=64, fanout=16, pct_ring=(40, 30, 20, 10),
+                       seed=3, sim_ms=100),
 }
 
 # The paper's own geometry (Sec. 2 and Table 1): columns of 1000 neurons (800
