@@ -562,12 +562,12 @@ __device__ __forceinline__ void deliver_ordered(const DevNet &n, const int *t_no
 }
 
 // One target's reverse entries [lo, hi), walked by a warp, kUnroll entries
-// per lane and round: the entries, then the sources' history words, then a
+// per lane and pass: the entries, then the sources' history words, then a
 // reduction of every non-zero amount into the entry's accumulator (no load:
 // an entry whose source did not fire inside the window costs its 4 or 8
-// bytes and nothing else).  The entries of the next round are loaded before
-// this round's histories are gathered, so that the two loads' latencies
-// overlap.  Returns whether the lane added into an accumulator.
+// bytes and nothing else).  The entries of the next pass are loaded before
+// the current pass's histories are gathered, so that the two loads'
+// latencies overlap.  Returns whether the lane added into an accumulator.
 template <bool kCompact>
 __device__ __forceinline__ bool ltp_walk(const DevNet &n, int64_t lo, int64_t hi, int lane, const int32_t *nb,
                                          const int32_t *s_lut, int tp)
